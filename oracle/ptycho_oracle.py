@@ -1,0 +1,333 @@
+"""FP64 CPU oracle of the multi-wavelength, multi-mode ptychography model.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously-correct
+statement of what the GPU library computes.  Only ``tests/``, ``__graft_entry__.smoke``
+and the CPU-baseline / reference legs of ``bench.py`` may import it; the library
+never calls it and shares no code with it.
+
+It follows the paper's universal model (Eq. 1) written as the composite of sub-models
+f1..f5 (Eq. 2): f1 scales the probe power by sigma_j, f2 shifts the object by the scan
+position s_j, f3 forms the exit wave P*O, f4 propagates to the detector, f5 applies the
+measurement effects (background, tilted-plane remap, mask).  The loss (amplitude MSE
+or Poisson, Section "Universal Ptychography Algorithm") is summed over frames and
+pixels; its gradient is the analytic adjoint of the same steps (the reverse pass that
+Fig. 1B describes).  Every frame is handled in an explicit loop.
+
+Readings of points where the paper is silent (each also recorded in the design notes):
+
+* propagation D_{lambda,z}: orthonormal 2D DFT with the zero frequency moved to
+  (F/2, F/2); each wavelength is sampled at its own object pixel size so all
+  wavelengths share one detector grid;
+* integer scan shift: the patch is O_l[y:y+F, x:x+F]; a patch outside the object is
+  an error (no wrap-around, no clamping);
+* tilted-plane remap: a fixed bilinear operator R from the model grid (uniform in
+  sample-plane spatial frequency) to the camera grid, derived from the camera being
+  perpendicular to the specular beam (Section "Experimental setup"); taps outside the
+  model grid remove the camera pixel from the mask;
+* background N(rho) lives on the model grid and is added before the remap;
+* losses: amplitude  sum (sqrt(I+eps) - sqrt(Ihat))^2, Poisson deviance
+  sum (I+eps) - Ihat - Ihat*log((I+eps)/Ihat) with 0*log(.) := 0; no normalisation;
+* gradient convention g = dL/dRe + i dL/dIm (complex parameters);
+* Adam acts on real and imaginary parts as separate real parameters.
+
+Parity pins: see ``tests/test_oracle_pins.py`` (brute-force DFT, Parseval, unitary
+mode-mixing and global-phase invariance, closed-form diffraction of plane waves,
+zero loss and zero gradient at noiseless truth, central finite differences, remap
+dot-product / identity / constant tests, the Adam first-step closed form and the
+paper's geometry numbers).  The tilted-plane remap formula itself is a reading of the
+cited geometry and is only partially pinned (identity limit, constants, adjointness,
+the paper's NA and pixel-ratio figures).
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+LOSS_KINDS = ("amplitude", "poisson")
+
+
+# ----------------------------------------------------------------------------
+# f1, f2, f3: probe power, object shift, exit wave  (Eq. 2)
+# ----------------------------------------------------------------------------
+
+def f1_power(P_lm: np.ndarray, sigma_j: float) -> np.ndarray:
+    """f1: scale the probe mode by the power coefficient sigma_j (Eq. 1)."""
+    return sigma_j * P_lm
+
+
+def f2_shift(O_l: np.ndarray, s_j: Sequence[int], F: int) -> np.ndarray:
+    """f2: the object seen through an F x F window whose corner sits at s_j = (row, col)."""
+    y, x = int(s_j[0]), int(s_j[1])
+    H, W = O_l.shape
+    if y < 0 or x < 0 or y + F > H or x + F > W:
+        raise ValueError(f"patch at ({y},{x}) of size {F} leaves the {H}x{W} object")
+    return O_l[y:y + F, x:x + F]
+
+
+def f3_interaction(P_scaled: np.ndarray, patch: np.ndarray) -> np.ndarray:
+    """f3: multiplicative exit wave psi = (sigma P) * O(r - s)."""
+    return P_scaled * patch
+
+
+# ----------------------------------------------------------------------------
+# f4: propagation to the detector
+# ----------------------------------------------------------------------------
+
+def f4_propagate(psi: np.ndarray) -> np.ndarray:
+    """f4: orthonormal 2D DFT, zero frequency moved to (F/2, F/2)."""
+    return np.fft.fftshift(np.fft.fft2(psi, norm="ortho"))
+
+
+def f4_adjoint(Psi: np.ndarray) -> np.ndarray:
+    """Adjoint (= inverse) of f4: undo the centring, orthonormal inverse 2D DFT."""
+    return np.fft.ifft2(np.fft.ifftshift(Psi), norm="ortho")
+
+
+# ----------------------------------------------------------------------------
+# tilted-plane remap (part of the measurement f5 in the in-model form)
+# ----------------------------------------------------------------------------
+
+class RemapTaps:
+    """Bilinear taps of the model-grid -> camera-grid remap for one geometry."""
+
+    def __init__(self, valid, i0, j0, wy, wx, yhat, xhat, db, da):
+        self.valid, self.i0, self.j0, self.wy, self.wx = valid, i0, j0, wy, wx
+        self.yhat, self.xhat = yhat, xhat
+        self.db, self.da = db, da      # model-grid spacings in direction cosines
+
+    @property
+    def F(self) -> int:
+        return self.valid.shape[0]
+
+
+def remap_taps(F: int, z: float, det_pixel: float, tilt_rad: float) -> RemapTaps:
+    """Where each camera pixel samples the model grid.
+
+    The camera is perpendicular to the specular beam at distance z.  Camera pixel
+    (y, x) sees the direction (X, Y, z) with X = (x - F/2) p, Y = (y - F/2) p.  In the
+    sample frame, tilted by alpha from the normal, its in-plane direction cosines are
+    a = X / R and b = (Y cos(alpha) + z sin(alpha)) / R - sin(alpha), R = |(X, Y, z)|.
+    The model grid is uniform in (b, a) with spacings (p/z) cos(alpha) and p/z, centred
+    on the specular direction, which reproduces the 3:1 pixel anisotropy reported for
+    the 70 degree geometry.  The fractional model index is
+    (b / db + F/2, a / da + F/2); the pixel is valid when all four bilinear taps fall
+    inside the grid.
+    """
+    c, s = math.cos(tilt_rad), math.sin(tilt_rad)
+    da = det_pixel / z
+    db = da * c
+    y, x = np.mgrid[0:F, 0:F].astype(np.float64)
+    X = (x - F / 2) * det_pixel
+    Y = (y - F / 2) * det_pixel
+    R = np.sqrt(X * X + Y * Y + z * z)
+    a = X / R
+    b = (Y * c + z * s) / R - s
+    yhat = b / db + F / 2
+    xhat = a / da + F / 2
+    valid = (yhat >= 0.0) & (yhat < F - 1) & (xhat >= 0.0) & (xhat < F - 1)
+    i0 = np.where(valid, np.floor(yhat), 0).astype(np.int64)
+    j0 = np.where(valid, np.floor(xhat), 0).astype(np.int64)
+    wy = np.where(valid, yhat - i0, 0.0)
+    wx = np.where(valid, xhat - j0, 0.0)
+    return RemapTaps(valid, i0, j0, wy, wx, yhat, xhat, db, da)
+
+
+def _tap_weights(taps: RemapTaps):
+    """The four (row, col, weight) taps of every camera pixel; weight 0 where invalid."""
+    i, j, u, v, ok = taps.i0, taps.j0, taps.wy, taps.wx, taps.valid
+    return [(i, j, np.where(ok, (1 - u) * (1 - v), 0.0)),
+            (i, j + 1, np.where(ok, (1 - u) * v, 0.0)),
+            (i + 1, j, np.where(ok, u * (1 - v), 0.0)),
+            (i + 1, j + 1, np.where(ok, u * v, 0.0))]
+
+
+def remap_apply(I_model: np.ndarray, taps: RemapTaps) -> np.ndarray:
+    """R: bilinear interpolation of the model-grid pattern at each camera pixel (0 if invalid)."""
+    out = np.zeros(taps.valid.shape)
+    for (ii, jj, w) in _tap_weights(taps):
+        out += w * I_model[ii, jj]
+    return out
+
+
+def remap_adjoint(D_cam: np.ndarray, taps: RemapTaps) -> np.ndarray:
+    """R^T: scatter each camera-pixel value back onto its four model-grid taps."""
+    out = np.zeros(taps.valid.shape)
+    for (ii, jj, w) in _tap_weights(taps):
+        np.add.at(out, (ii, jj), w * D_cam)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# f5: measurement (background, remap) and the mask
+# ----------------------------------------------------------------------------
+
+def f5_measure(I_sum: np.ndarray, bg: Optional[np.ndarray], taps: Optional[RemapTaps]) -> np.ndarray:
+    """f5: add the common background on the model grid, then remap to the camera grid."""
+    I = I_sum if bg is None else I_sum + bg
+    return I if taps is None else remap_apply(I, taps)
+
+
+def frame_mask(mask: Optional[np.ndarray], j: int, F: int, taps: Optional[RemapTaps]) -> np.ndarray:
+    """Pixels that enter the loss for frame j: user mask AND remap validity."""
+    if mask is None:
+        mk = np.ones((F, F), bool)
+    elif mask.ndim == 3:
+        mk = mask[j] != 0
+    else:
+        mk = mask != 0
+    if taps is not None:
+        mk = mk & taps.valid
+    return mk
+
+
+# ----------------------------------------------------------------------------
+# losses (Section "Universal Ptychography Algorithm")
+# ----------------------------------------------------------------------------
+
+def loss_terms(I: np.ndarray, Ihat: np.ndarray, kind: str, eps: float) -> np.ndarray:
+    """Per-pixel loss.  amplitude: (sqrt(I+eps) - sqrt(Ihat))^2; Poisson: deviance."""
+    Ie = I + eps
+    Ihat = Ihat.astype(np.float64)
+    if kind == "amplitude":
+        return (np.sqrt(Ie) - np.sqrt(Ihat)) ** 2
+    if kind == "poisson":
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lg = np.where(Ihat > 0, Ihat * np.log(Ie / np.where(Ihat > 0, Ihat, 1.0)), 0.0)
+        return Ie - Ihat - lg
+    raise ValueError(kind)
+
+
+def loss_derivative(I: np.ndarray, Ihat: np.ndarray, kind: str, eps: float) -> np.ndarray:
+    """dL/dI per pixel.  amplitude: 1 - sqrt(Ihat)/sqrt(I+eps); Poisson: 1 - Ihat/(I+eps)."""
+    Ie = I + eps
+    Ihat = Ihat.astype(np.float64)
+    if kind == "amplitude":
+        return 1.0 - np.sqrt(Ihat) / np.sqrt(Ie)
+    if kind == "poisson":
+        return 1.0 - Ihat / Ie
+    raise ValueError(kind)
+
+
+# ----------------------------------------------------------------------------
+# the model (Eq. 1) and its adjoint
+# ----------------------------------------------------------------------------
+
+def _sigma(sigma, j):
+    return 1.0 if sigma is None else float(sigma[j])
+
+
+def frame_fields(O, P, pos, j, sigma=None):
+    """Exit waves and propagated fields Psi_{j,l,m} for one frame (f1..f4)."""
+    L, M, F = P.shape[0], P.shape[1], P.shape[2]
+    s = _sigma(sigma, j)
+    patches, Psi = [], np.empty((L, M, F, F), np.complex128)
+    for l in range(L):
+        p = f2_shift(O[l], pos[l][j], F)
+        patches.append(p)
+        for m in range(M):
+            Psi[l, m] = f4_propagate(f3_interaction(f1_power(P[l, m], s), p))
+    return patches, Psi
+
+
+def predict_frame(O, P, pos, j, sigma=None, bg=None, taps=None) -> np.ndarray:
+    """Eq. 1 for frame j: remap( sum_l sum_m |D[sigma_j P_lm O_l(r - s_j)]|^2 + N )."""
+    _, Psi = frame_fields(O, P, pos, j, sigma)
+    I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
+    return f5_measure(I_sum, bg, taps)
+
+
+def predict(O, P, pos, sigma=None, bg=None, taps=None, frames=None) -> np.ndarray:
+    """Predicted camera-grid patterns for the requested frames (default: all)."""
+    J = pos.shape[1]
+    frames = range(J) if frames is None else frames
+    return np.stack([predict_frame(O, P, pos, j, sigma, bg, taps) for j in frames])
+
+
+def loss(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None) -> float:
+    """Total loss over the requested frames and their masked pixels."""
+    F = P.shape[2]
+    J = pos.shape[1]
+    frames = range(J) if frames is None else frames
+    total = 0.0
+    for j in frames:
+        Ic = predict_frame(O, P, pos, j, sigma, bg, taps)
+        mk = frame_mask(mask, j, F, taps)
+        total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
+    return total
+
+
+def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None):
+    """Loss and its gradient (dL/dRe + i dL/dIm) with respect to every O_l and P_lm.
+
+    For each frame: forward fields Psi_{lm}; I = sum |Psi|^2 (+bg); camera pattern R I;
+    D = mask * dL/dI_cam; G = R^T D; chi_{lm} = f4^-1(2 G Psi_{lm}) is the gradient
+    with respect to the exit wave; then grad P_lm += conj(sigma p_l) chi_lm and
+    grad O_l[patch] += conj(sigma P_lm) chi_lm.
+    """
+    L, M, F = P.shape[0], P.shape[1], P.shape[2]
+    J = pos.shape[1]
+    frames = range(J) if frames is None else frames
+    gO = [np.zeros_like(o, dtype=np.complex128) for o in O]
+    gP = np.zeros_like(P, dtype=np.complex128)
+    total = 0.0
+    for j in frames:
+        s = _sigma(sigma, j)
+        patches, Psi = frame_fields(O, P, pos, j, sigma)
+        I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
+        Ic = f5_measure(I_sum, bg, taps)
+        mk = frame_mask(mask, j, F, taps)
+        total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
+        with np.errstate(divide="ignore", invalid="ignore"):
+            D = np.where(mk, loss_derivative(Ic, Imeas[j], kind, eps), 0.0)
+        G = D if taps is None else remap_adjoint(D, taps)
+        for l in range(L):
+            y, x = int(pos[l][j][0]), int(pos[l][j][1])
+            for m in range(M):
+                chi = f4_adjoint(2.0 * G * Psi[l, m])
+                gP[l, m] += np.conj(s * patches[l]) * chi
+                gO[l][y:y + F, x:x + F] += np.conj(s * P[l, m]) * chi
+    return total, gO, gP
+
+
+# ----------------------------------------------------------------------------
+# Adam (Kingma & Ba), real and imaginary parts as separate real parameters
+# ----------------------------------------------------------------------------
+
+class AdamState:
+    def __init__(self, shapes_O: List[tuple], shape_P: tuple):
+        self.mO = [np.zeros(s + (2,)) for s in shapes_O]
+        self.vO = [np.zeros(s + (2,)) for s in shapes_O]
+        self.mP = np.zeros(shape_P + (2,))
+        self.vP = np.zeros(shape_P + (2,))
+        self.t = 0
+
+
+def _as_real(z: np.ndarray) -> np.ndarray:
+    return np.stack([z.real, z.imag], axis=-1)
+
+
+def adam_update(theta: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int,
+                lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam step on a complex array; m and v are [..., 2] real arrays updated in place."""
+    gr = _as_real(g)
+    m *= b1
+    m += (1.0 - b1) * gr
+    v *= b2
+    v += (1.0 - b2) * gr * gr
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    upd = lr * mhat / (np.sqrt(vhat) + eps)
+    return theta - (upd[..., 0] + 1j * upd[..., 1])
+
+
+def step(O, P, pos, Imeas, kind, eps, state: AdamState, lr_O: float, lr_P: float,
+         b1=0.9, b2=0.999, adam_eps=1e-8, sigma=None, bg=None, mask=None, taps=None, frames=None):
+    """One optimisation step: loss and gradient over ``frames``, then Adam on O and P."""
+    total, gO, gP = gradient(O, P, pos, Imeas, kind, eps, sigma, bg, mask, taps, frames)
+    state.t += 1
+    O_new = [adam_update(O[l], gO[l], state.mO[l], state.vO[l], state.t, lr_O, b1, b2, adam_eps)
+             for l in range(len(O))]
+    P_new = adam_update(P, gP, state.mP, state.vP, state.t, lr_P, b1, b2, adam_eps)
+    return total, O_new, P_new

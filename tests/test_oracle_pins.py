@@ -1,0 +1,378 @@
+"""Pins of the FP64 oracle against facts fixed by mathematics and by the paper.
+
+None of these re-types the oracle's formula: each checks it against an independent
+statement (a brute-force sum, a closed form, an invariance of Eq. 1, a finite
+difference, an adjoint identity, or a number printed in the paper).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from synthetic import workloads as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(np.asarray(b).ravel()), 1e-300))
+
+
+def crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ----------------------------------------------------------------------------
+# f4: propagation
+# ----------------------------------------------------------------------------
+
+def brute_dft2_centred(x):
+    """O(F^4) DFT with exp(-2 pi i k n / F), 1/F scaling, zero frequency stored at F/2."""
+    F = x.shape[0]
+    out = np.zeros((F, F), np.complex128)
+    for k1 in range(F):
+        for k2 in range(F):
+            acc = 0j
+            for n1 in range(F):
+                for n2 in range(F):
+                    acc += x[n1, n2] * complex(math.cos(-2 * math.pi * (k1 * n1 + k2 * n2) / F),
+                                               math.sin(-2 * math.pi * (k1 * n1 + k2 * n2) / F))
+            out[(k1 + F // 2) % F, (k2 + F // 2) % F] = acc / F
+    return out
+
+
+def test_propagate_matches_bruteforce_dft_8x8():
+    rng = np.random.default_rng(0)
+    x = crandn(rng, 8, 8)
+    assert rel(orc.f4_propagate(x), brute_dft2_centred(x)) < 1e-12
+
+
+def test_propagate_adjoint_is_inverse_and_adjoint():
+    rng = np.random.default_rng(1)
+    x, y = crandn(rng, 16, 16), crandn(rng, 16, 16)
+    assert rel(orc.f4_adjoint(orc.f4_propagate(x)), x) < 1e-12
+    # <A x, y> = <x, A^H y>
+    lhs = np.vdot(y, orc.f4_propagate(x))
+    rhs = np.vdot(orc.f4_adjoint(y), x)
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_parseval():
+    rng = np.random.default_rng(2)
+    for F in (8, 64, 256):
+        x = crandn(rng, F, F)
+        assert abs((np.abs(orc.f4_propagate(x)) ** 2).sum() / (np.abs(x) ** 2).sum() - 1) < 1e-12
+
+
+def test_plane_wave_diffracts_to_one_pixel():
+    """A flat probe on an object e^{2 pi i (u r + v c)/F} puts all power at (F/2+u, F/2+v)."""
+    F, u, v = 32, 3, -5
+    H = 48
+    rr, cc = np.mgrid[0:H, 0:H]
+    O = np.exp(2j * math.pi * (u * rr + v * cc) / F)
+    P = np.full((1, 1, F, F), 0.7 + 0.2j)
+    pos = np.array([[[4, 9]]], np.int32)
+    I = orc.predict([O], P, pos)[0]
+    expect = np.zeros((F, F))
+    expect[F // 2 + u, F // 2 + v] = F * F * abs(0.7 + 0.2j) ** 2
+    assert np.abs(I - expect).max() < 1e-9 * expect.max()
+
+
+def test_point_probe_gives_flat_pattern_of_the_right_object_pixel():
+    """A probe that is a delta at (r0, c0) diffracts to |P O(y+r0, x+c0)|^2 / F^2 everywhere."""
+    rng = np.random.default_rng(3)
+    F, H, W = 16, 30, 34
+    O = crandn(rng, H, W)
+    P = np.zeros((1, 1, F, F), np.complex128)
+    r0, c0 = 3, 11
+    P[0, 0, r0, c0] = 2.0 - 1.0j
+    y, x = 7, 2
+    I = orc.predict([O], P, np.array([[[y, x]]], np.int32))[0]
+    flat = abs((2.0 - 1.0j) * O[y + r0, x + c0]) ** 2 / F ** 2
+    assert np.abs(I - flat).max() < 1e-12 * flat
+
+
+def test_single_mode_frame_equals_textbook_bruteforce():
+    """L = M = 1 reduces to |DFT(P . O_patch)|^2 with the patch read pixel by pixel."""
+    rng = np.random.default_rng(4)
+    F, H, W = 8, 13, 15
+    O = crandn(rng, H, W)
+    P = crandn(rng, 1, 1, F, F)
+    y, x = 4, 6
+    ex = np.zeros((F, F), np.complex128)
+    for r in range(F):
+        for c in range(F):
+            ex[r, c] = P[0, 0, r, c] * O[y + r, x + c]
+    expect = np.abs(brute_dft2_centred(ex)) ** 2
+    got = orc.predict([O], P, np.array([[[y, x]]], np.int32))[0]
+    assert rel(got, expect) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Eq. 1 structure: incoherent sums and invariances
+# ----------------------------------------------------------------------------
+
+def test_incoherent_sum_is_sum_of_single_mode_patterns():
+    w = syn.tiny_workload(F=16, L=2, M=3, seed=11)
+    full = orc.predict(w.O_true, w.P_true, w.pos)
+    acc = np.zeros_like(full)
+    for l in range(w.L):
+        for m in range(w.M):
+            acc += orc.predict([w.O_true[l]], w.P_true[l:l + 1, m:m + 1], w.pos[l:l + 1])
+    assert rel(full, acc) < 1e-12
+
+
+def test_unitary_mode_mixing_and_global_phase_invariance():
+    w = syn.tiny_workload(F=16, L=2, M=3, seed=12)
+    rng = np.random.default_rng(5)
+    base = orc.predict(w.O_true, w.P_true, w.pos)
+    P2 = np.empty_like(w.P_true)
+    for l in range(w.L):
+        q, _ = np.linalg.qr(crandn(rng, w.M, w.M))
+        P2[l] = np.einsum("ab,bij->aij", q, w.P_true[l])
+    assert rel(orc.predict(w.O_true, P2, w.pos), base) < 1e-12
+    assert rel(orc.predict(w.O_true, w.P_true * np.exp(1.234j), w.pos), base) < 1e-12
+    # and O -> c O, P -> P / c
+    c = 1.7 * np.exp(0.3j)
+    assert rel(orc.predict([o * c for o in w.O_true], w.P_true / c, w.pos), base) < 1e-12
+
+
+def test_power_coefficient_scales_the_pattern_quadratically():
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=13)
+    sigma = np.linspace(0.5, 1.5, w.J)
+    a = orc.predict(w.O_true, w.P_true, w.pos, sigma=sigma)
+    b = orc.predict(w.O_true, w.P_true, w.pos)
+    assert rel(a, b * (sigma ** 2)[:, None, None]) < 1e-12
+
+
+def test_patch_outside_object_is_an_error():
+    w = syn.tiny_workload(F=16, L=1, M=1, seed=14)
+    pos = w.pos.copy()
+    pos[0, 0] = (w.obj_shapes[0][0] - 15, 0)
+    with pytest.raises(ValueError):
+        orc.predict(w.O_true, w.P_true, pos)
+    pos[0, 0] = (-1, 0)
+    with pytest.raises(ValueError):
+        orc.predict(w.O_true, w.P_true, pos)
+
+
+# ----------------------------------------------------------------------------
+# losses
+# ----------------------------------------------------------------------------
+
+def test_loss_derivative_matches_finite_difference_per_pixel():
+    rng = np.random.default_rng(6)
+    I = rng.uniform(0.5, 20, size=200)
+    Ih = np.floor(rng.uniform(0, 25, size=200))
+    for kind in orc.LOSS_KINDS:
+        h = 1e-6
+        fd = (orc.loss_terms(I + h, Ih, kind, 1e-3) - orc.loss_terms(I - h, Ih, kind, 1e-3)) / (2 * h)
+        assert rel(orc.loss_derivative(I, Ih, kind, 1e-3), fd) < 1e-7
+
+
+def test_poisson_deviance_differs_from_plain_nll_by_a_constant():
+    rng = np.random.default_rng(7)
+    Ih = np.floor(rng.uniform(0, 25, size=100))
+    I1, I2 = rng.uniform(0.5, 20, size=100), rng.uniform(0.5, 20, size=100)
+    nll = lambda I: I - Ih * np.log(I)  # noqa: E731
+    d1 = orc.loss_terms(I1, Ih, "poisson", 0.0) - nll(I1)
+    d2 = orc.loss_terms(I2, Ih, "poisson", 0.0) - nll(I2)
+    assert np.abs(d1 - d2).max() < 1e-10
+    # and the deviance vanishes at I = Ihat (0 log 0 := 0 at empty pixels)
+    assert np.abs(orc.loss_terms(Ih, Ih, "poisson", 0.0)).max() < 1e-12
+
+
+def test_amplitude_loss_is_squared_modulus_difference():
+    I = np.array([4.0, 9.0, 0.25])
+    Ih = np.array([1.0, 16.0, 0.0])
+    assert np.allclose(orc.loss_terms(I, Ih, "amplitude", 0.0), [1.0, 1.0, 0.25], atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", orc.LOSS_KINDS)
+@pytest.mark.parametrize("remap", [False, True])
+def test_zero_loss_and_zero_gradient_at_noiseless_truth(kind, remap):
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=15, remap=remap, with_bg=True, with_sigma=True)
+    taps = orc.remap_taps(w.F, 2e-3, 15e-6, math.radians(70)) if remap else None
+    Ih = orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps)
+    L, gO, gP = orc.gradient(w.O_true, w.P_true, w.pos, Ih, kind, 0.0, w.sigma, w.bg, None, taps)
+    assert abs(L) < 1e-18 * max(1.0, float(Ih.sum()))
+    assert max(np.abs(g).max() for g in gO) < 1e-12
+    assert np.abs(gP).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# gradient: central finite differences
+# ----------------------------------------------------------------------------
+
+def _fd_case(kind, remap, with_mask):
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=21, remap=remap, loss=kind, with_sigma=True,
+                          with_bg=True)
+    taps = orc.remap_taps(w.F, 2e-3, 15e-6, math.radians(70)) if remap else None
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps), 3)
+    mask = None
+    if with_mask:
+        mask = (np.random.default_rng(9).uniform(size=(w.J, w.F, w.F)) > 0.2).astype(np.uint8)
+    return w, taps, Ih, mask
+
+
+@pytest.mark.parametrize("kind", orc.LOSS_KINDS)
+@pytest.mark.parametrize("remap,with_mask", [(False, False), (True, True)])
+def test_gradient_matches_central_finite_differences(kind, remap, with_mask):
+    w, taps, Ih, mask = _fd_case(kind, remap, with_mask)
+    eps = 1e-3
+    args = (w.pos, Ih, kind, eps, w.sigma, w.bg, mask, taps)
+    _, gO, gP = orc.gradient(w.O0, w.P0, *args)
+    rng = np.random.default_rng(10)
+    h = 1e-5
+    L0 = abs(orc.loss(w.O0, w.P0, *args))
+    noise = 50 * 2.2e-16 * L0 / h        # rounding floor of a central difference
+    checks = 0
+    for _ in range(6):
+        l = int(rng.integers(w.L))
+        # an object pixel inside the scanned area
+        y, x = w.pos[l][int(rng.integers(w.J))] + rng.integers(0, w.F, size=2)
+        for comp in (1.0, 1.0j):
+            Op = [o.copy() for o in w.O0]
+            Om = [o.copy() for o in w.O0]
+            Op[l][y, x] += h * comp
+            Om[l][y, x] -= h * comp
+            fd = (orc.loss(Op, w.P0, *args) - orc.loss(Om, w.P0, *args)) / (2 * h)
+            an = gO[l][y, x].real if comp == 1.0 else gO[l][y, x].imag
+            assert abs(fd - an) <= 1e-6 * abs(an) + noise, (fd, an, noise)
+            checks += 1
+        m = int(rng.integers(w.M))
+        r, c = rng.integers(0, w.F, size=2)
+        for comp in (1.0, 1.0j):
+            Pp, Pm = w.P0.copy(), w.P0.copy()
+            Pp[l, m, r, c] += h * comp
+            Pm[l, m, r, c] -= h * comp
+            fd = (orc.loss(w.O0, Pp, *args) - orc.loss(w.O0, Pm, *args)) / (2 * h)
+            an = gP[l, m, r, c].real if comp == 1.0 else gP[l, m, r, c].imag
+            assert abs(fd - an) <= 1e-6 * abs(an) + noise, (fd, an, noise)
+            checks += 1
+    assert checks == 24
+
+
+def test_gradient_directional_derivative():
+    """dL along a random complex direction d equals Re<g, d> summed over all parameters."""
+    w, taps, Ih, mask = _fd_case("poisson", True, True)
+    args = (w.pos, Ih, "poisson", 1e-3, w.sigma, w.bg, mask, taps)
+    _, gO, gP = orc.gradient(w.O0, w.P0, *args)
+    rng = np.random.default_rng(11)
+    dO = [crandn(rng, *o.shape) for o in w.O0]
+    dP = crandn(rng, *w.P0.shape)
+    h = 1e-6
+    Lp = orc.loss([o + h * d for o, d in zip(w.O0, dO)], w.P0 + h * dP, *args)
+    Lm = orc.loss([o - h * d for o, d in zip(w.O0, dO)], w.P0 - h * dP, *args)
+    fd = (Lp - Lm) / (2 * h)
+    an = sum(np.real(np.vdot(g, d)) for g, d in zip(gO, dO)) + np.real(np.vdot(gP, dP))
+    assert abs(fd - an) < 1e-6 * abs(an)
+
+
+def test_gradient_vanishes_outside_the_scanned_area():
+    w, taps, Ih, mask = _fd_case("amplitude", False, False)
+    _, gO, _ = orc.gradient(w.O0, w.P0, w.pos, Ih, "amplitude", 1e-3, w.sigma, w.bg, None, None)
+    for l in range(w.L):
+        cov = np.zeros(w.obj_shapes[l], bool)
+        for j in range(w.J):
+            y, x = w.pos[l][j]
+            cov[y:y + w.F, x:x + w.F] = True
+        assert np.abs(gO[l][~cov]).max() == 0.0
+
+
+def test_masked_pixels_do_not_enter_the_loss():
+    w, taps, Ih, mask = _fd_case("amplitude", False, True)
+    a = orc.loss(w.O0, w.P0, w.pos, Ih, "amplitude", 1e-3, w.sigma, w.bg, mask, None)
+    Ih2 = Ih.copy()
+    Ih2[mask == 0] += 1000.0
+    b = orc.loss(w.O0, w.P0, w.pos, Ih2, "amplitude", 1e-3, w.sigma, w.bg, mask, None)
+    assert a == b
+
+
+# ----------------------------------------------------------------------------
+# tilted-plane remap
+# ----------------------------------------------------------------------------
+
+def test_remap_dot_product_identity():
+    taps = orc.remap_taps(64, 0.02, 15e-6, math.radians(70))
+    rng = np.random.default_rng(12)
+    x, y = rng.standard_normal((64, 64)), rng.standard_normal((64, 64))
+    lhs = float((orc.remap_apply(x, taps) * y).sum())
+    rhs = float((x * orc.remap_adjoint(y, taps)).sum())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_remap_is_near_identity_without_tilt():
+    taps = orc.remap_taps(64, 88e-3, 15e-6, 0.0)
+    assert taps.valid.all()
+    yy, xx = np.mgrid[0:64, 0:64]
+    assert np.abs(taps.yhat - yy).max() < 1e-3
+    assert np.abs(taps.xhat - xx).max() < 1e-3
+    rng = np.random.default_rng(13)
+    I = rng.uniform(size=(64, 64))
+    assert np.abs(orc.remap_apply(I, taps) - I).max() < 2e-3
+
+
+def test_remap_keeps_a_constant_inside_the_field_of_view():
+    taps = orc.remap_taps(64, 0.02, 15e-6, math.radians(70))
+    out = orc.remap_apply(np.full((64, 64), 3.25), taps)
+    assert not taps.valid.all() and taps.valid.any()
+    assert np.abs(out[taps.valid] - 3.25).max() < 1e-12
+    assert (out[~taps.valid] == 0).all()
+    # the specular pixel maps onto itself
+    assert taps.yhat[32, 32] == pytest.approx(32.0, abs=1e-9)
+    assert taps.xhat[32, 32] == pytest.approx(32.0, abs=1e-12)
+
+
+def test_remap_geometry_against_the_paper_numbers():
+    """NA, tilt-corrected pixel ratio and resolution printed in the paper."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_geometry.json")))
+    F = g["camera_pixels"]["value"]
+    z, p = g["z_m"]["value"], g["det_pixel_m"]["value"]
+    alpha = math.radians(g["tilt_deg"]["value"])
+    taps = orc.remap_taps(F, z, p, alpha)
+    # direction cosine along the untilted axis at the camera edge = detection NA
+    na_x = abs(taps.xhat[F // 2, 0] - F / 2) * (p / z)
+    assert na_x == pytest.approx(g["na"]["value"][0], rel=0.02)
+    # the tilt-corrected grid is 15 um x 5 um: model spacing along the tilt / across it
+    px = g["tilt_corrected_pixel_um"]["value"]
+    assert taps.db / taps.da == pytest.approx(px[1] / px[0], rel=0.04)
+    # the specular pixel maps to the grid centre and rows near it map one to one
+    assert taps.yhat[F // 2, F // 2] == pytest.approx(F / 2, abs=1e-6)
+    assert taps.yhat[F // 2 + 1, F // 2] - taps.yhat[F // 2, F // 2] == pytest.approx(1.0, abs=1e-3)
+    # diffraction-limited resolution lambda / (2 NA)
+    assert g["lambda_m"]["value"] / (2 * na_x) == pytest.approx(g["resolution_m"]["value"], rel=0.10)
+
+
+# ----------------------------------------------------------------------------
+# Adam
+# ----------------------------------------------------------------------------
+
+def test_adam_first_step_closed_form():
+    rng = np.random.default_rng(14)
+    th = crandn(rng, 5, 7)
+    g = crandn(rng, 5, 7)
+    m = np.zeros((5, 7, 2))
+    v = np.zeros((5, 7, 2))
+    lr, eps = 0.01, 1e-8
+    out = orc.adam_update(th, g, m, v, 1, lr, 0.9, 0.999, eps)
+    exp = th - lr * (g.real / (np.abs(g.real) + eps) + 1j * g.imag / (np.abs(g.imag) + eps))
+    assert np.abs(out - exp).max() < 1e-15
+    assert np.allclose(m[..., 0], 0.1 * g.real) and np.allclose(v[..., 1], 0.001 * g.imag ** 2)
+
+
+def test_adam_second_step_against_hand_expansion():
+    g1, g2 = 0.3, -0.7
+    th = np.array([1.0 + 0j])
+    m, v = np.zeros((1, 2)), np.zeros((1, 2))
+    th = orc.adam_update(th, np.array([g1 + 0j]), m, v, 1, 0.1)
+    th = orc.adam_update(th, np.array([g2 + 0j]), m, v, 2, 0.1)
+    m2 = 0.9 * 0.1 * g1 + 0.1 * g2
+    v2 = 0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2
+    step2 = 0.1 * (m2 / (1 - 0.81)) / (math.sqrt(v2 / (1 - 0.999 ** 2)) + 1e-8)
+    exp = 1.0 - 0.1 * g1 / (abs(g1) + 1e-8) - step2
+    assert abs(th[0].real - exp) < 1e-14 and th[0].imag == 0.0
