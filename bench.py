@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused forward + adjoint + Adam step.
+
+Workload (default): the wavelength-multiplexed multi-mode reflection case with 3
+wavelengths (1 : 1.1 : 1.2) x 4 probe modes, 256 x 256 frames, 400 jittered scan
+positions, 768 x 768 objects, tilted-plane remap and Poisson loss.  One *step* is one
+``ptycho_step`` over all 400 positions: forward model, loss, adjoint, object/probe
+gradients and Adam.  One *evaluation* is the forward + adjoint of one (position,
+wavelength, mode) triple, so a step is 400 * 3 * 4 = 4800 evaluations.
+
+Synthetic, seeded inputs stand in for the paper's EUV dataset.  ``--impl reference``
+times the FP64 CPU oracle (the only reference available) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint frame·mode·λ evals/s, % roofline; p50/p99 site-iteration latency"
+UNIT = "evals/s"
+L2_BYTES = 126 * 1024 * 1024
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 flop/FMA
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="config2", help="config1 | config2 | config4 | config3:F,M,L")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str):
+    from synthetic import workloads as syn
+    if name == "config1":
+        return syn.config1()
+    if name == "config2":
+        return syn.config2()
+    if name == "config4":
+        return syn.config4()
+    if name.startswith("config3:"):
+        F, M, L = (int(v) for v in name.split(":")[1].split(","))
+        return syn.config3(F, M, L)
+    raise SystemExit(f"unknown config {name}")
+
+
+def workload_config(w, name):
+    return {"workload": f"{name}: {w.L} wavelengths x {w.M} probe modes, {w.F}x{w.F} frames, {w.J} positions, "
+                        f"objects {w.obj_shapes[0][0]}x{w.obj_shapes[0][1]}, "
+                        f"{'tilted-plane remap' if w.geom.remap else 'no remap'}, {w.loss} loss",
+            "frames": w.F, "wavelengths": w.L, "modes": w.M, "positions": w.J,
+            "evals_per_step": w.n_evals}
+
+
+# --------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[1].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[1].split(".")[1]) if "." in parts[1] else 0.0
+                    rows.append(dict(ts=ts, sm=float(parts[2]), smax=float(parts[3]),
+                                     power=float(parts[4]) if parts[4] not in ("[N/A]", "N/A") else None,
+                                     reasons={"hw_slowdown": parts[6], "hw_thermal_slowdown": parts[7],
+                                              "sw_thermal_slowdown": parts[8], "sw_power_cap": parts[9]}))
+                except Exception:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "note": "nvidia-smi unavailable"}
+        win = [r for r in rows if self.t0 is not None and self.t0 - 0.05 <= r["ts"] <= self.t1 + 0.05]
+        note = "samples inside the timed region"
+        if len(win) < 3:
+            win = [r for r in rows if self.t0 is not None and self.t0 - 1.0 <= r["ts"] <= self.t1 + 1.0] or rows
+            note = "timed region shorter than the sampling interval: samples within 1 s of it"
+        reasons = sorted({k for r in win for k, v in r["reasons"].items() if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r["sm"] for r in win), "sm_max_mhz": max(r["smax"] for r in win),
+                "reasons": reasons, "samples": len(win),
+                "power_w_max": max((r["power"] for r in win if r["power"] is not None), default=None), "note": note}
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------------------
+def oracle_evals_per_s(w, n_pos: int, repeat: int = 1, seed: int = 0):
+    """Time the oracle's loss + gradient + Adam on n_pos positions; returns (evals/s, seconds, evals)."""
+    from oracle import ptycho_oracle as orc
+    from synthetic import workloads as syn
+    taps = orc.remap_taps(w.F, w.geom.z, w.geom.det_pixel, w.geom.tilt_rad) if w.geom.remap else None
+    rng = np.random.default_rng(seed)
+    frames = sorted(rng.choice(w.J, size=n_pos, replace=False).tolist())
+    clean = np.zeros((w.J, w.F, w.F))
+    clean[frames] = orc.predict(w.O_true, w.P_true, w.pos, None, None, taps, frames=frames)
+    Ih = syn.poisson_measure(clean, 5)
+    eps = 1e-9 * float(Ih[frames].mean())
+    st = orc.AdamState([o.shape for o in w.O0], w.P0.shape)
+    O, P = w.O0, w.P0
+    t0 = time.perf_counter()
+    for _ in range(repeat):
+        _, O, P = orc.step(O, P, w.pos, Ih, w.loss, eps, st, 1e-3, 1e-3, taps=taps, frames=frames)
+    dt = time.perf_counter() - t0
+    ev = repeat * n_pos * w.L * w.M
+    return ev / dt, dt, ev
+
+
+def cpu_threads_used() -> int:
+    # numpy's FFT (pocketfft) runs on one thread; the oracle makes no threaded calls
+    return 1
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    w = make_workload(args.config)
+    _, t1, _ = oracle_evals_per_s(w, 1)                         # calibration: one position
+    budget = 150.0
+    per_step = max(1, min(w.J, int(budget / max(1, args.steps + args.warmup) / max(t1, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_evals_per_s(w, per_step, seed=1)
+    tot_t, tot_e = 0.0, 0
+    for k in range(args.steps):
+        _, dt, ev = oracle_evals_per_s(w, per_step, seed=2 + k)
+        tot_t += dt
+        tot_e += ev
+    v = tot_e / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args.config),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+                             "sample": f"{per_step} of {w.J} positions per step ({per_step * w.L * w.M} evals): "
+                                       "FP64 NumPy loss + gradient + Adam"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2311_14780_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(f"{workload}:{kernel}")
+    if not e or e.get("csrc_sha") != csrc_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_flops_per_eval(F: int) -> float:
+    """Two orthonormal 2D DFTs (forward + adjoint) at 5 N log2 N flops each, N = F^2."""
+    return 2 * 5.0 * F * F * math.log2(F * F)
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2311_14780_gb300 import AdamState, pack_objects, plan_for
+    from synthetic import workloads as syn
+
+    w = make_workload(args.config)
+    # measured data: our forward model on the ground truth, plus Poisson noise (not a parity claim)
+    plan_true = plan_for(w, eps=0.0)
+    Ot = pack_objects(w.O_true, dev)
+    Pt = torch.as_tensor(w.P_true, dtype=torch.complex64, device=dev).contiguous()
+    I_clean = plan_true.forward(Ot, Pt).cpu().numpy()
+    plan_true.close()
+    Ih = syn.poisson_measure(I_clean, 1234 + rank)
+    eps = syn.default_eps(Ih)
+    plan = plan_for(w, eps=eps)
+    O = pack_objects(w.O0, dev)
+    P = torch.as_tensor(w.P0, dtype=torch.complex64, device=dev).contiguous()
+    Im = torch.as_tensor(Ih, device=dev).contiguous()
+    st = AdamState(plan, lr_O=1e-3, lr_P=1e-3)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(4 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    evals = w.n_evals
+
+    def step():
+        plan.step(st, O, P, Im, loss_out=loss)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = plan.last_launches
+
+    # ---- timed region: per-step events, L2 flushed between steps --------------------
+    clocks = ClockSampler(local)
+    time.sleep(0.2)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = float(sum(step_ms))
+    if dist:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    clk = clocks.stop()
+    value = evals * args.steps * world / (t_ms / 1e3)
+
+    # ---- per-kernel event timing for the roofline (same workload, same stream) --------
+    plan.profile(True)
+    prof_steps = max(3, min(args.steps, 50))
+    for _ in range(prof_steps):
+        step()
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    flops_eval = algorithmic_flops_per_eval(w.F)
+    # each of the four DFT passes (row fwd, col fwd, col adj, row adj) carries a quarter of
+    # the algorithmic flops of every evaluation it processes
+    fft_kernels = ("row_fwd", "col_fwd", "col_adj", "row_adj")
+    dom = max(prof, key=lambda k: prof[k][0])
+    kern_ms, kern_n = prof[dom]
+    units_per_launch = evals * prof_steps / max(1, kern_n) if dom in fft_kernels else 0
+    roof = None
+    if dom in fft_kernels and kern_n:
+        per_launch_flops = 0.25 * flops_eval * units_per_launch
+        achieved = per_launch_flops / (kern_ms / kern_n / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": ncu_traffic(dom, args.config),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no FP32 figure in "
+                               "MEASURED_PEAKS.json)",
+                "units_per_launch": units_per_launch, "flops_per_unit": 0.25 * flops_eval,
+                "avg_launch_ms": kern_ms / kern_n}
+    step_total = sum(v[0] for v in prof.values()) / prof_steps
+    step_flops = flops_eval * evals
+    kernels = {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps,
+                   "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))} for k, v in prof.items() if v[1]}
+
+    # ---- end to end through the public API with host buffers --------------------------
+    e2e = None
+    if not args.no_e2e:
+        Ih_pinned = torch.as_tensor(Ih).pin_memory()
+        loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+        e_steps = max(3, min(args.steps, 50))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            Im.copy_(Ih_pinned, non_blocking=True)
+            step()
+            loss_host.copy_(loss, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        if dist:
+            tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": evals * e_steps * world / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(Ih_pinned.numel() * 4), "d2h_bytes_per_step": 8,
+               "note": "pinned host I_meas copied to the GPU every step; loss read back every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, t1, _ = oracle_evals_per_s(w, 1)
+        n_pos = max(1, min(w.J, int(args.cpu_seconds / max(t1, 1e-3))))
+        v_cpu, dt, ev = oracle_evals_per_s(w, n_pos, seed=3)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+               "sample": f"{n_pos} of {w.J} positions ({ev} evals, {dt:.1f} s): FP64 NumPy loss + gradient + Adam"}
+
+    if rank == 0:
+        cfg = workload_config(w, args.config)
+        cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "l2": "L2 flushed (512 MB write) before every timed step; per-step I_meas 105 MB + "
+                          "parameters and Adam state exceed the 126 MB L2"})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (loss sum f64)", "data": "synthetic",
+                "config": cfg, "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
+                "roofline": roof, "step_flop_rate_tflops": step_flops / (t_ms / args.steps / 1e3) / 1e12,
+                "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99))}
+        print(json.dumps(line))
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

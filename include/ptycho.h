@@ -1,0 +1,172 @@
+/*
+ * ptycho.h - C ABI of the GB300 multi-wavelength, multi-mode ptychography hot path.
+ *
+ * The library evaluates the universal ptychography model of arXiv 2311.14780, Eq. 1,
+ *
+ *   I_j = M[ sum_l sum_m | D_{lambda_l,z}[ sigma_j P_lm(r) O_l(r - s_j) ] |^2 + N ],
+ *
+ * written as the composite f5(f4(f3(f1(sigma_j), f2(s_j)))) of Eq. 2, scores it with the
+ * amplitude (MSE on the modulus) or Poisson loss of the section "Universal Ptychography
+ * Algorithm based on Automatic Differentiation", returns the analytic gradient that the
+ * paper obtains by reverse-mode differentiation (Fig. 1B), and applies Adam.  One sample
+ * mode per wavelength (N = 1 in Eq. 1), as in the paper's reconstructions.
+ *
+ * Conventions shared by every entry point
+ *   - Complex arrays are complex64: interleaved (re, im) float pairs, row-major.
+ *   - Array arguments of compute calls are DEVICE pointers owned by the caller.  The
+ *     library never frees them and only reads inputs / overwrites outputs.
+ *   - Objects of all wavelengths are packed into one buffer: O_l starts at complex offset
+ *     sum_{l' < l} obj_h[l'] * obj_w[l'] and is obj_h[l] x obj_w[l] row-major.
+ *   - Probes: P[L][M][F][F].  Predicted / measured patterns: [J][F][F] float, camera grid,
+ *     zero frequency at (F/2, F/2).
+ *   - Propagation D is the orthonormal 2D DFT with the zero frequency moved to the centre;
+ *     each wavelength is sampled at its own object pixel size (lambda_l z / (F p)), so all
+ *     wavelengths share one detector grid.
+ *   - Gradients use g = dL/dRe + i dL/dIm for every complex parameter.
+ *   - Compute calls are asynchronous on ``stream`` (a cudaStream_t passed as void*; NULL =
+ *     the legacy default stream) and must be issued on the device that was current when
+ *     the plan was created.  Calls on one plan share its workspace: do not run two calls
+ *     of the same plan concurrently on different streams.
+ *   - Return value: 0 on success, a negative PTYCHO_E* code otherwise (text through
+ *     ptycho_strerror).  Argument errors are detected on the host before any launch.
+ */
+#ifndef PTYCHO_GB300_H
+#define PTYCHO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTYCHO_OK 0
+#define PTYCHO_EINVAL (-1)       /* bad shape, size, NULL pointer or option            */
+#define PTYCHO_ERANGE (-2)       /* a scan position puts a patch outside its object   */
+#define PTYCHO_ENOMEM (-3)       /* device allocation of the plan workspace failed     */
+#define PTYCHO_ECUDA (-4)        /* a CUDA call or kernel launch failed                */
+#define PTYCHO_ETIMEDOUT (-5)    /* a bounded device wait ran out (serving loop)       */
+#define PTYCHO_EUNSUPPORTED (-6) /* frame size not in {64, 128, 256, 512}, L > 16      */
+
+#define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
+#define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */
+
+typedef struct ptycho_plan ptycho_plan_t;
+
+/* Problem description (all pointers are HOST pointers, read during ptycho_plan_create). */
+typedef struct {
+  int32_t L;                /* wavelengths (Eq. 1 index l), 1..16                       */
+  int32_t M;                /* incoherent probe modes per wavelength (index m), >= 1    */
+  int32_t F;                /* frame side: 64, 128, 256 or 512                          */
+  int32_t J;                /* scan positions (the paper's index k), >= 1               */
+  const int32_t* obj_h;     /* [L] object rows, >= F                                    */
+  const int32_t* obj_w;     /* [L] object columns, >= F                                 */
+  const int32_t* pos;       /* [L][J][2] (row, col) of each patch's top-left corner in
+                               wavelength-l object pixels: the integer scan shift s_j of
+                               f2 (Eq. 2).  0 <= row <= obj_h[l] - F, same for col.    */
+  const double* lambda;     /* [L] wavelengths in metres (recorded; may be NULL)        */
+  double z;                 /* sample-camera distance, metres (88 mm in the paper)      */
+  double det_pixel;         /* camera pixel pitch, metres (15 um)                       */
+  double tilt_rad;          /* angle of incidence from the surface normal (70 degrees)  */
+  int32_t remap;            /* 1: apply the tilted-plane remap inside f5; 0: identity   */
+  int32_t loss;             /* PTYCHO_LOSS_AMPLITUDE or PTYCHO_LOSS_POISSON             */
+  float eps;                /* intensity floor added to I in the loss and its gradient  */
+  int64_t scratch_bytes;    /* L2-resident FFT scratch budget; 0 = library default      */
+} ptycho_geom_t;
+
+/* Adam state (Kingma & Ba), cited by the paper as its optimiser.  Real and imaginary
+ * parts are separate real parameters.  m and v are DEVICE arrays with the layout of the
+ * parameter they belong to (2 floats per complex element), zero-initialised by the caller. */
+typedef struct {
+  float lr_O, lr_P;         /* step sizes of the objects and of the probes              */
+  float beta1, beta2, eps;  /* 0.9, 0.999, 1e-8 are the usual values                    */
+  int32_t t;                /* steps taken so far; ptycho_step increments it            */
+  float* mO; float* vO;     /* [2 * numel(O)]                                           */
+  float* mP; float* vP;     /* [2 * numel(P)]                                           */
+} ptycho_adam_t;
+
+/* Validates the geometry and every scan position (PTYCHO_ERANGE names an out-of-object
+ * patch: no wrap-around, no clamping), builds the remap operator R (bilinear, four taps
+ * per camera pixel; camera pixels whose taps leave the model grid are masked) and its
+ * exact transpose, the twiddle table, and allocates the device workspace.  The plan owns
+ * everything it allocates.  Returns PTYCHO_ENOMEM if the workspace cannot be allocated. */
+int ptycho_plan_create(const ptycho_geom_t* geom, ptycho_plan_t** out);
+
+/* Frees the plan and its workspace (synchronises the device first).  NULL is accepted. */
+int ptycho_plan_destroy(ptycho_plan_t* plan);
+
+/* Bytes of device memory owned by the plan; complex element counts of O and P. */
+int64_t ptycho_plan_workspace_bytes(const ptycho_plan_t* plan);
+int64_t ptycho_plan_numel_O(const ptycho_plan_t* plan);
+int64_t ptycho_plan_numel_P(const ptycho_plan_t* plan);
+
+/* Forward model, Eq. 1 / Eq. 2: I_pred[j] for every scan position j.
+ *   O      packed objects (complex64)           P    [L][M][F][F] complex64
+ *   sigma  [J] power coefficients of f1, or NULL (all 1)
+ *   bg     [F][F] background N on the model grid (added before the remap), or NULL
+ *   I_pred [J][F][F] out: camera-grid prediction; pixels the remap cannot reach are 0 */
+int ptycho_forward(ptycho_plan_t* plan, const float* O, const float* P, const float* sigma,
+                   const float* bg, float* I_pred, void* stream);
+
+/* Loss of the selected positions (section "Universal Ptychography Algorithm"):
+ *   I_meas    [J][F][F] measured patterns (camera grid)
+ *   mask      NULL (all pixels), [F][F] (mask_per_frame = 0) or [J][F][F] (= 1); nonzero
+ *             = used.  Pixels the remap cannot reach are excluded in addition.
+ *   batch_idx DEVICE int32 list of positions to include, or NULL for all J in order
+ *   nbatch    entries of batch_idx (ignored when batch_idx is NULL)
+ *   loss_dev  DEVICE double, out: sum over positions and used pixels (FP64 reduction) */
+int ptycho_loss(ptycho_plan_t* plan, const float* O, const float* P, const float* sigma,
+                const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
+                const int32_t* batch_idx, int nbatch, double* loss_dev, void* stream);
+
+/* Loss and its gradient with respect to every O_l and P_lm (the reverse pass of Fig. 1B),
+ * summed over the selected positions.  gO (numel(O) complex) and gP (numel(P) complex)
+ * are OVERWRITTEN.  The propagated fields are kept in the plan's scratch between the
+ * forward and adjoint passes when they fit its budget, and recomputed otherwise.
+ * Arguments as for ptycho_loss; loss_dev may be NULL. */
+int ptycho_adjoint(ptycho_plan_t* plan, const float* O, const float* P, const float* sigma,
+                   const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
+                   const int32_t* batch_idx, int nbatch, float* gO, float* gP, double* loss_dev,
+                   void* stream);
+
+/* One optimisation step on a batch of positions ("per batch" updates, Fig. 2 caption):
+ * ptycho_adjoint into plan-owned gradient buffers, then Adam on O (lr_O) and P (lr_P) in
+ * place.  state->t is incremented on the host before the update. */
+int ptycho_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, const float* sigma,
+                const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
+                const int32_t* batch_idx, int nbatch, double* loss_dev, void* stream);
+
+/* Number of kernel launches issued by the most recent compute call on this plan. */
+int64_t ptycho_plan_last_launches(const ptycho_plan_t* plan);
+
+/* Device-side status of the plan since the previous query, then cleared.  Bit 0
+ * (PTYCHO_STATUS_BAD_INDEX): a batch_idx entry was outside [0, J); that position was
+ * skipped.  Synchronises the device (call it outside the timed loop). */
+#define PTYCHO_STATUS_BAD_INDEX 1
+int ptycho_plan_status(ptycho_plan_t* plan, int32_t* flags);
+
+/* Opt-in per-kernel timing.  While enabled, every launch of a compute call is bracketed
+ * by a CUDA event pair recorded on the call's stream.  ptycho_plan_profile_read waits for
+ * the recorded events and fills, per kernel kind (PTYCHO_K_*), the summed device time in
+ * ms and the launch count since profiling was enabled or last read; then it restarts.
+ * ms and launches are HOST arrays of PTYCHO_NUM_KERNELS entries. */
+#define PTYCHO_K_ROW_FWD 0       /* exit wave + row DFT                                  */
+#define PTYCHO_K_COL_FWD 1       /* column DFT + |Psi|^2 mode sum                         */
+#define PTYCHO_K_LOSS 2          /* remap + mask + loss partials + dL/dI                  */
+#define PTYCHO_K_COL_ADJ 3       /* R^T, (2/F) G Psi, inverse column DFT                  */
+#define PTYCHO_K_ROW_ADJ 4       /* inverse row DFT + probe gradient                      */
+#define PTYCHO_K_OBJ_GRAD 5      /* tile-owned object-gradient sum                        */
+#define PTYCHO_K_LOSS_REDUCE 6   /* FP64 loss reduction                                   */
+#define PTYCHO_K_ADAM 7          /* Adam update                                          */
+#define PTYCHO_NUM_KERNELS 8
+int ptycho_plan_profile(ptycho_plan_t* plan, int enable);
+int ptycho_plan_profile_read(ptycho_plan_t* plan, double* ms, int64_t* launches);
+const char* ptycho_kernel_name(int kind);
+
+/* Static text for a return code. */
+const char* ptycho_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTYCHO_GB300_H */

@@ -1,0 +1,80 @@
+"""ctypes declarations of the C ABI in ``include/ptycho.h``.
+
+Loading never falls back to anything: if the CUDA library has not been built, every
+entry point raises.  Build it with ``__graft_entry__.build()`` or
+``python paper_2311_14780_gb300/build.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int32), ("M", ctypes.c_int32), ("F", ctypes.c_int32), ("J", ctypes.c_int32),
+        ("obj_h", c_int32_p), ("obj_w", c_int32_p), ("pos", c_int32_p), ("lam", c_double_p),
+        ("z", ctypes.c_double), ("det_pixel", ctypes.c_double), ("tilt_rad", ctypes.c_double),
+        ("remap", ctypes.c_int32), ("loss", ctypes.c_int32), ("eps", ctypes.c_float),
+        ("scratch_bytes", ctypes.c_int64),
+    ]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [
+        ("lr_O", ctypes.c_float), ("lr_P", ctypes.c_float), ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("t", ctypes.c_int32),
+        ("mO", ctypes.c_void_p), ("vO", ctypes.c_void_p), ("mP", ctypes.c_void_p), ("vP", ctypes.c_void_p),
+    ]
+
+
+# (name, restype, argtypes) of every exported entry point
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = [
+    ("ptycho_plan_create", _I, [ctypes.POINTER(Geom), ctypes.POINTER(_VP)]),
+    ("ptycho_plan_destroy", _I, [_VP]),
+    ("ptycho_plan_workspace_bytes", ctypes.c_int64, [_VP]),
+    ("ptycho_plan_numel_O", ctypes.c_int64, [_VP]),
+    ("ptycho_plan_numel_P", ctypes.c_int64, [_VP]),
+    ("ptycho_plan_last_launches", ctypes.c_int64, [_VP]),
+    ("ptycho_forward", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ptycho_loss", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
+    ("ptycho_adjoint", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP]),
+    ("ptycho_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
+    ("ptycho_plan_status", _I, [_VP, c_int32_p]),
+    ("ptycho_plan_profile", _I, [_VP, _I]),
+    ("ptycho_plan_profile_read", _I, [_VP, c_double_p, ctypes.POINTER(ctypes.c_int64)]),
+    ("ptycho_kernel_name", ctypes.c_char_p, [_I]),
+    ("ptycho_strerror", ctypes.c_char_p, [_I]),
+]
+
+NUM_KERNELS = 8
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"CUDA library {path} is missing: build it with __graft_entry__.build(); "
+                "there is no CPU fallback")
+        h = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = h
+    return _LIB

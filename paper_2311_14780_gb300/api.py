@@ -1,0 +1,261 @@
+"""Python front end of the C ABI: argument marshalling only.
+
+Every computation happens in the CUDA library; this module checks tensor dtypes,
+shapes and devices, passes raw device pointers and the current torch stream, and turns
+return codes into exceptions.  Names follow the C entry points (ptycho_forward,
+ptycho_loss, ptycho_adjoint, ptycho_step).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native
+
+LOSS_CODES = {"amplitude": 0, "poisson": 1}
+
+
+class PtychoError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _native.lib().ptycho_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise PtychoError(code, where)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def pack_objects(objs: Sequence, device="cuda") -> torch.Tensor:
+    """Pack per-wavelength objects into the library's flat complex64 layout."""
+    flat = [torch.as_tensor(np.asarray(o), dtype=torch.complex64).reshape(-1) for o in objs]
+    return torch.cat(flat).to(device)
+
+
+def unpack_objects(flat: torch.Tensor, shapes) -> list:
+    out, off = [], 0
+    for (h, w) in shapes:
+        out.append(flat[off:off + h * w].reshape(h, w))
+        off += h * w
+    return out
+
+
+class Plan:
+    """A validated problem geometry with its device workspace (``ptycho_plan_t``)."""
+
+    def __init__(self, F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = "amplitude",
+                 eps: float = 0.0, remap: bool = False, z: float = 88e-3, det_pixel: float = 15e-6,
+                 tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0):
+        self.F, self.L, self.M, self.J = int(F), int(L), int(M), int(J)
+        self.obj_shapes = [(int(h), int(w)) for (h, w) in obj_shapes]
+        self.loss_kind = loss
+        self._h = np.ascontiguousarray([s[0] for s in self.obj_shapes], dtype=np.int32)
+        self._w = np.ascontiguousarray([s[1] for s in self.obj_shapes], dtype=np.int32)
+        self._pos = np.ascontiguousarray(np.asarray(pos, dtype=np.int32).reshape(L, J, 2))
+        self._lam = None if lambdas is None else np.ascontiguousarray(lambdas, dtype=np.float64)
+        g = _native.Geom()
+        g.L, g.M, g.F, g.J = self.L, self.M, self.F, self.J
+        g.obj_h = self._h.ctypes.data_as(_native.c_int32_p)
+        g.obj_w = self._w.ctypes.data_as(_native.c_int32_p)
+        g.pos = self._pos.ctypes.data_as(_native.c_int32_p)
+        g.lam = None if self._lam is None else self._lam.ctypes.data_as(_native.c_double_p)
+        g.z, g.det_pixel, g.tilt_rad = float(z), float(det_pixel), float(tilt_rad)
+        g.remap = 1 if remap else 0
+        g.loss = LOSS_CODES[loss]
+        g.eps = float(eps)
+        g.scratch_bytes = int(scratch_bytes)
+        self._geom = g
+        h = ctypes.c_void_p()
+        _check(_native.lib().ptycho_plan_create(ctypes.byref(g), ctypes.byref(h)), "ptycho_plan_create")
+        self._h_plan = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    # -- properties ----------------------------------------------------------------
+    @property
+    def handle(self):
+        return self._h_plan
+
+    @property
+    def numel_O(self) -> int:
+        return int(_native.lib().ptycho_plan_numel_O(self._h_plan))
+
+    @property
+    def numel_P(self) -> int:
+        return int(_native.lib().ptycho_plan_numel_P(self._h_plan))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(_native.lib().ptycho_plan_workspace_bytes(self._h_plan))
+
+    @property
+    def last_launches(self) -> int:
+        return int(_native.lib().ptycho_plan_last_launches(self._h_plan))
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) per-kernel event timing of this plan's launches."""
+        _check(_native.lib().ptycho_plan_profile(self._h_plan, 1 if enable else 0), "ptycho_plan_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since profiling started or was last read."""
+        ms = (ctypes.c_double * _native.NUM_KERNELS)()
+        n = (ctypes.c_int64 * _native.NUM_KERNELS)()
+        _check(_native.lib().ptycho_plan_profile_read(self._h_plan, ms, n), "ptycho_plan_profile_read")
+        return {_native.lib().ptycho_kernel_name(k).decode(): (float(ms[k]), int(n[k]))
+                for k in range(_native.NUM_KERNELS)}
+
+    def status(self) -> int:
+        """Device status flags since the last query (synchronises; bit 0 = bad batch index)."""
+        v = ctypes.c_int32(0)
+        _check(_native.lib().ptycho_plan_status(self._h_plan, ctypes.byref(v)), "ptycho_plan_status")
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "_h_plan", None) is not None and self._h_plan.value:
+            _native.lib().ptycho_plan_destroy(self._h_plan)
+            self._h_plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- argument checks -----------------------------------------------------------
+    def _c64(self, t: torch.Tensor, n: int, name: str):
+        if t.dtype != torch.complex64 or not t.is_contiguous() or t.device != self.device or t.numel() != n:
+            raise ValueError(f"{name}: need a contiguous complex64 tensor of {n} elements on {self.device}")
+        return torch.view_as_real(t)
+
+    def _f32(self, t, n: int, name: str):
+        if t is None:
+            return None
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.device != self.device or t.numel() != n:
+            raise ValueError(f"{name}: need a contiguous float32 tensor of {n} elements on {self.device}")
+        return t
+
+    def _mask(self, mask):
+        FF = self.F * self.F
+        if mask is None:
+            return None, 0
+        if mask.dtype != torch.uint8 or not mask.is_contiguous() or mask.device != self.device:
+            raise ValueError("mask: need a contiguous uint8 tensor on the plan's device")
+        if mask.numel() == FF:
+            return mask, 0
+        if mask.numel() == self.J * FF:
+            return mask, 1
+        raise ValueError("mask: need F*F or J*F*F elements")
+
+    def _batch(self, batch):
+        if batch is None:
+            return None, 0
+        if batch.dtype != torch.int32 or not batch.is_contiguous() or batch.device != self.device:
+            raise ValueError("batch: need a contiguous int32 tensor on the plan's device")
+        return batch, int(batch.numel())
+
+    # -- compute calls ---------------------------------------------------------------
+    def forward(self, O, P, sigma=None, bg=None, out=None, stream=None) -> torch.Tensor:
+        """ptycho_forward: predicted camera-grid patterns [J, F, F] float32."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        if out is None:
+            out = torch.empty((self.J, self.F, self.F), dtype=torch.float32, device=self.device)
+        self._f32(out, self.J * FF, "out")
+        rc = _native.lib().ptycho_forward(self._h_plan, _ptr(Or), _ptr(Pr), _ptr(self._f32(sigma, self.J, "sigma")),
+                                          _ptr(self._f32(bg, FF, "bg")), _ptr(out), _stream_handle(stream))
+        _check(rc, "ptycho_forward")
+        return out
+
+    def loss(self, O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, out=None, stream=None):
+        """ptycho_loss: FP64 loss (a 1-element device tensor)."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        m, mpf = self._mask(mask)
+        bt, nb = self._batch(batch)
+        if out is None:
+            out = torch.zeros(1, dtype=torch.float64, device=self.device)
+        rc = _native.lib().ptycho_loss(self._h_plan, _ptr(Or), _ptr(Pr), _ptr(self._f32(sigma, self.J, "sigma")),
+                                       _ptr(self._f32(bg, FF, "bg")), _ptr(self._f32(Imeas, self.J * FF, "Imeas")),
+                                       _ptr(m), mpf, _ptr(bt), nb, _ptr(out), _stream_handle(stream))
+        _check(rc, "ptycho_loss")
+        return out
+
+    def adjoint(self, O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, gO=None, gP=None, loss_out=None,
+                stream=None):
+        """ptycho_adjoint: (loss, grad O, grad P); gradients use dL/dRe + i dL/dIm."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        m, mpf = self._mask(mask)
+        bt, nb = self._batch(batch)
+        if gO is None:
+            gO = torch.empty(self.numel_O, dtype=torch.complex64, device=self.device)
+        if gP is None:
+            gP = torch.empty(P.shape, dtype=torch.complex64, device=self.device)
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float64, device=self.device)
+        gOr, gPr = self._c64(gO, self.numel_O, "gO"), self._c64(gP, self.numel_P, "gP")
+        rc = _native.lib().ptycho_adjoint(self._h_plan, _ptr(Or), _ptr(Pr), _ptr(self._f32(sigma, self.J, "sigma")),
+                                          _ptr(self._f32(bg, FF, "bg")),
+                                          _ptr(self._f32(Imeas, self.J * FF, "Imeas")), _ptr(m), mpf, _ptr(bt), nb,
+                                          _ptr(gOr), _ptr(gPr), _ptr(loss_out), _stream_handle(stream))
+        _check(rc, "ptycho_adjoint")
+        return loss_out, gO, gP
+
+    def step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, loss_out=None,
+             stream=None):
+        """ptycho_step: adjoint + fused Adam on O and P in place; returns the FP64 loss tensor."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        m, mpf = self._mask(mask)
+        bt, nb = self._batch(batch)
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float64, device=self.device)
+        st = state.c_struct()
+        rc = _native.lib().ptycho_step(self._h_plan, ctypes.byref(st), _ptr(Or), _ptr(Pr),
+                                       _ptr(self._f32(sigma, self.J, "sigma")), _ptr(self._f32(bg, FF, "bg")),
+                                       _ptr(self._f32(Imeas, self.J * FF, "Imeas")), _ptr(m), mpf, _ptr(bt), nb,
+                                       _ptr(loss_out), _stream_handle(stream))
+        _check(rc, "ptycho_step")
+        state.t = int(st.t)
+        return loss_out
+
+
+class AdamState:
+    """Adam moments for O and P (device tensors, 2 floats per complex element)."""
+
+    def __init__(self, plan: Plan, lr_O: float, lr_P: float, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+        dev = plan.device
+        self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps = lr_O, lr_P, beta1, beta2, eps
+        self.t = 0
+        self.mO = torch.zeros(2 * plan.numel_O, dtype=torch.float32, device=dev)
+        self.vO = torch.zeros_like(self.mO)
+        self.mP = torch.zeros(2 * plan.numel_P, dtype=torch.float32, device=dev)
+        self.vP = torch.zeros_like(self.mP)
+
+    def c_struct(self) -> _native.Adam:
+        s = _native.Adam()
+        s.lr_O, s.lr_P, s.beta1, s.beta2, s.eps, s.t = self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps, self.t
+        s.mO, s.vO = self.mO.data_ptr(), self.vO.data_ptr()
+        s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
+        return s
+
+
+def plan_for(w, **kw) -> Plan:
+    """Plan for a :class:`synthetic.workloads.Workload`-like object (attribute access only)."""
+    return Plan(w.F, w.L, w.M, w.J, w.obj_shapes, w.pos, loss=kw.pop("loss", w.loss),
+                remap=kw.pop("remap", w.geom.remap), z=kw.pop("z", w.geom.z),
+                det_pixel=kw.pop("det_pixel", w.geom.det_pixel), tilt_rad=kw.pop("tilt_rad", w.geom.tilt_rad),
+                lambdas=w.geom.lambdas, **kw)

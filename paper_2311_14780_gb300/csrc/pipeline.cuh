@@ -1,0 +1,140 @@
+// Orchestration of one compute call for a fixed frame size F: loops over position batches
+// and mode chunks and launches the kernels of kernels.cuh on the caller's stream.
+#pragma once
+#include "plan.h"
+
+namespace ptycho {
+
+// Launch a kernel of the given kind on stream st, count it, bracket it with profiling
+// events when enabled, and turn a launch failure into PTYCHO_ECUDA.
+#define PTY_LAUNCH(p, kind, st, ...)                                 \
+  do {                                                               \
+    const long long pty_ev = prof_begin((p), (kind), (st));          \
+    __VA_ARGS__;                                                     \
+    ++(p).last_launches;                                             \
+    if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;      \
+    prof_end((p), pty_ev, (st));                                     \
+  } while (0)
+
+template <int F>
+int prepare_kernels() {
+  static int done = 0;
+  if (done) return PTYCHO_OK;
+  const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
+  if (e != cudaSuccess) return PTYCHO_ECUDA;
+  done = 1;
+  return PTYCHO_OK;
+}
+
+template <int F>
+int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
+  int rc = prepare_kernels<F>();
+  if (rc) return rc;
+  constexpr int FF = F * F;
+  const bool grad = c.kind == CallKind::Adjoint;
+  const bool need_loss = c.kind != CallKind::Forward;
+  const bool store = grad && p.store;   // keep Psi only when an adjoint follows
+
+  KArgs a{};
+  a.L = p.L; a.M = p.M; a.F = F; a.J = p.J;
+  a.pos = p.d_pos;
+  for (int l = 0; l < p.L; ++l) { a.obj_off[l] = p.obj_off[l]; a.obj_h[l] = p.obj_h[l]; a.obj_w[l] = p.obj_w[l]; }
+  a.bidx = c.bidx;
+  a.nbatch = c.nbatch;
+  a.sigma = c.sigma;
+  a.tw = p.d_tw;
+  a.C = p.C;
+  a.MG = p.MG;
+  a.G = p.G;
+  a.status = p.d_status;
+
+  LossArgs la{};
+  la.Ipart = p.d_Ipart;
+  la.bg = c.bg;
+  la.tap_base = p.d_tap_base;
+  la.tap_w = p.d_tap_w;
+  la.Imeas = c.Imeas;
+  la.mask = c.mask;
+  la.mask_per_frame = c.mask_per_frame;
+  la.eps = p.eps;
+  la.loss_kind = p.loss_kind;
+  la.D = grad ? p.d_D : nullptr;
+  la.loss_part = need_loss ? p.d_loss_part : nullptr;
+  la.I_pred = c.kind == CallKind::Forward ? c.I_pred : nullptr;
+  la.remap = p.remap;
+
+  AdjArgs aa{};
+  aa.D = p.d_D;
+  aa.rt_ptr = p.d_rt_ptr;
+  aa.rt_idx = p.d_rt_idx;
+  aa.rt_w = p.d_rt_w;
+  aa.remap = p.remap;
+
+  p.last_launches = 0;
+  if (grad) {
+    if (cudaMemsetAsync(c.gO, 0, sizeof(float2) * p.O_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
+    if (cudaMemsetAsync(c.gP, 0, sizeof(float2) * p.P_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
+  }
+  const int LM = p.L * p.M;
+  const dim3 row_blk(RowCfg<F>::threads), col_blk(ColCfg<F>::threads);
+  const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
+  const int obj_blocks = (2 * p.sms + p.L - 1) / p.L;
+
+  for (int off = 0; off < c.nbatch; off += p.B) {
+    a.batch_off = off;
+    a.nb = (c.nbatch - off < p.B) ? (c.nbatch - off) : p.B;
+    // forward: all chunks accumulate the model intensity
+    for (int ch = 0; ch < p.nchunks; ++ch) {
+      a.chunk_base = ch * p.C;
+      a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
+      PTY_LAUNCH(p, kRowFwd, st,
+                 k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len, a.nb), row_blk, RowCfg<F>::smem, st>>>(
+                     c.O, c.P, p.d_S, a));
+      if (store)
+        PTY_LAUNCH(p, kColFwd, st,
+                   k_col_fwd<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, st>>>(
+                       p.d_S, p.d_Ipart, a, ch == 0));
+      else
+        PTY_LAUNCH(p, kColFwd, st,
+                   k_col_fwd<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, st>>>(
+                       p.d_S, p.d_Ipart, a, ch == 0));
+    }
+    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, st>>>(a, la));
+    if (!grad) continue;
+    for (int ch = 0; ch < p.nchunks; ++ch) {
+      a.chunk_base = ch * p.C;
+      a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
+      if (store) {
+        PTY_LAUNCH(p, kColAdj, st,
+                   k_col_adj<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
+      } else {
+        PTY_LAUNCH(p, kRowFwd, st,
+                   k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len, a.nb), row_blk, RowCfg<F>::smem, st>>>(
+                       c.O, c.P, p.d_S, a));
+        PTY_LAUNCH(p, kColAdj, st,
+                   k_col_adj<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
+      }
+      PTY_LAUNCH(p, kRowAdj, st,
+                 k_row_adj<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len), row_blk, RowCfg<F>::smem, st>>>(
+                     c.O, c.P, p.d_S, c.gP, a));
+      PTY_LAUNCH(p, kObjGrad, st, k_obj_grad<F><<<dim3(obj_blocks, p.L), 256, 0, st>>>(p.d_S, c.gO, a));
+    }
+  }
+  if (need_loss) {
+    double* out = c.loss;
+    if (out) {
+      PTY_LAUNCH(p, kLossReduce, st,
+                 k_loss_reduce<<<1, 256, 0, st>>>(p.d_loss_part, (long long)c.nbatch * (FF / kLossThreads), out));
+    }
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace ptycho

@@ -1,0 +1,85 @@
+// Host-side plan: geometry, validated positions, remap tables, batching decisions and the
+// device workspace.  Shared by the C-ABI front end and the per-frame-size pipelines.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/ptycho.h"
+#include "kernels.cuh"
+
+struct ptycho_plan {
+  int dev = 0;
+  int sms = 0;
+  int L = 0, M = 0, F = 0, J = 0;
+  int remap = 0, loss_kind = 0;
+  float eps = 0.f;
+  int obj_h[ptycho::kMaxL] = {}, obj_w[ptycho::kMaxL] = {};
+  long long obj_off[ptycho::kMaxL] = {};
+  long long O_numel = 0, P_numel = 0;          // complex elements
+  std::vector<int32_t> pos_host;               // [L][J][2]
+
+  // batching: B positions per batch, modes split into chunks of C, columns kernels use
+  // G groups of MG modes; store = 1 keeps Psi in S between the forward and the adjoint.
+  int store = 1, B = 1, C = 1, nchunks = 1, G = 1, MG = 1;
+  long long scratch_budget = 0;
+
+  // device workspace (all owned by the plan)
+  int32_t* d_pos = nullptr;
+  int32_t* d_ident = nullptr;
+  float2* d_tw = nullptr;
+  int32_t* d_tap_base = nullptr;
+  float2* d_tap_w = nullptr;
+  int32_t* d_rt_ptr = nullptr;
+  int32_t* d_rt_idx = nullptr;
+  float* d_rt_w = nullptr;
+  float2* d_S = nullptr;
+  float* d_Ipart = nullptr;
+  float* d_D = nullptr;
+  double* d_loss_part = nullptr;
+  float2* d_gO = nullptr;
+  float2* d_gP = nullptr;
+  int* d_status = nullptr;                     // device status word, see ptycho_plan_status
+  long long bytes = 0;
+  long long last_launches = 0;
+
+  // opt-in per-kernel timing: an event pair around every launch, read back on request
+  int prof = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;                    // kind of the launch of each event pair
+};
+
+namespace ptycho {
+
+enum class CallKind { Forward, Loss, Adjoint };
+
+struct CallArgs {
+  CallKind kind;
+  const float2* O;
+  const float2* P;
+  const float* sigma;
+  const float* bg;
+  const float* Imeas;
+  const uint8_t* mask;
+  int mask_per_frame;
+  const int32_t* bidx;     // device; never null here (the front end substitutes d_ident)
+  int nbatch;
+  float* I_pred;
+  float2* gO;
+  float2* gP;
+  double* loss;
+};
+
+// Kernel kinds reported by ptycho_plan_profile_read (order matches PTYCHO_K_* in ptycho.h).
+enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kNumKinds };
+
+// Records the start event of a profiled launch (no-op unless profiling); returns the pair index.
+long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);
+void prof_end(ptycho_plan& p, long long idx, cudaStream_t st);
+
+// Defined once per frame size in kern_<F>.cu.
+template <int F> int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st);
+template <int F> int prepare_kernels();
+
+}  // namespace ptycho

@@ -1,0 +1,471 @@
+// C-ABI front end: geometry and position validation, the tilted-plane remap tables, the
+// batching decision, workspace allocation and dispatch to the frame-size pipelines.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "plan.h"
+
+namespace ptycho {
+
+// Fixed-order FP64 sum of the per-block loss partials (one block).
+__global__ void __launch_bounds__(256) k_loss_reduce(const double* __restrict__ part, long long n, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += 256) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// Adam (Kingma & Ba) on real parameters; c1, c2 are the bias corrections 1/(1-beta^t).
+__global__ void __launch_bounds__(256)
+k_adam(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
+       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float g = grad[i];
+    const float mi = fmaf(b1, m[i], (1.f - b1) * g);
+    const float vi = fmaf(b2, v[i], (1.f - b2) * g * g);
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st) {
+  if (!p.prof) return -1;
+  const size_t i = p.ev_used;
+  while (p.ev_pool.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    p.ev_pool.push_back(e);
+  }
+  p.ev_used = i + 1;
+  p.ev_kind.resize(p.ev_used);
+  p.ev_kind[i] = kind;
+  cudaEventRecord(p.ev_pool[2 * i], st);
+  return (long long)i;
+}
+
+void prof_end(ptycho_plan& p, long long idx, cudaStream_t st) {
+  if (idx >= 0) cudaEventRecord(p.ev_pool[2 * idx + 1], st);
+}
+
+}  // namespace ptycho
+
+using ptycho::CallArgs;
+using ptycho::CallKind;
+
+namespace {
+
+constexpr long long kDefaultScratch = 64ll << 20;   // L2-resident FFT scratch (L2 = 126 MiB)
+constexpr double kPi = 3.14159265358979323846;
+
+bool supported_F(int F) { return F == 64 || F == 128 || F == 256 || F == 512; }
+
+template <class T>
+int dalloc(ptycho_plan* p, T** ptr, long long count) {
+  if (count <= 0) { *ptr = nullptr; return PTYCHO_OK; }
+  const size_t bytes = sizeof(T) * (size_t)count;
+  if (cudaMalloc((void**)ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return PTYCHO_ENOMEM;
+  }
+  p->bytes += (long long)bytes;
+  return PTYCHO_OK;
+}
+
+template <class T>
+int upload(T* dst, const T* src, long long count) {
+  if (count <= 0) return PTYCHO_OK;
+  return cudaMemcpy(dst, src, sizeof(T) * (size_t)count, cudaMemcpyHostToDevice) == cudaSuccess ? PTYCHO_OK
+                                                                                              : PTYCHO_ECUDA;
+}
+
+void free_plan(ptycho_plan* p) {
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
+                  p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_loss_part, p->d_gO, p->d_gP, p->d_status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+// Tilted-plane remap R (model grid -> camera grid), following the reflection geometry of the
+// section "Experimental setup": camera perpendicular to the specular beam at distance z,
+// sample tilted by alpha from the normal.  Camera pixel (y, x) looks along (X, Y, z) with
+// X = (x - F/2) p, Y = (y - F/2) p; its sample-frame direction cosines are a = X / R and
+// b = (Y cos a + z sin a) / R - sin a.  The model grid is uniform in (b, a) with spacings
+// (p/z) cos(alpha) and p/z around the specular direction.  Each camera pixel takes the
+// bilinear interpolation of its four surrounding model pixels; it is invalid (masked) when
+// they leave the grid.  Index decisions are taken in FP64.
+void build_remap(int F, double z, double p, double alpha, std::vector<int32_t>& base, std::vector<float2>& w,
+                 std::vector<int32_t>& rt_ptr, std::vector<int32_t>& rt_idx, std::vector<float>& rt_w) {
+  const double c = cos(alpha), s = sin(alpha);
+  const double da = p / z, db = da * c;
+  const int FF = F * F;
+  base.assign(FF, -1);
+  w.assign(FF, make_float2(0.f, 0.f));
+  std::vector<double> wy(FF, 0.0), wx(FF, 0.0);
+  for (int y = 0; y < F; ++y) {
+    for (int x = 0; x < F; ++x) {
+      const double X = (x - F / 2.0) * p;
+      const double Y = (y - F / 2.0) * p;
+      const double R = sqrt(X * X + Y * Y + z * z);
+      const double a = X / R;
+      const double b = (Y * c + z * s) / R - s;
+      const double yh = b / db + F / 2.0;
+      const double xh = a / da + F / 2.0;
+      if (yh >= 0.0 && yh < F - 1 && xh >= 0.0 && xh < F - 1) {
+        const int iy = (int)floor(yh), ix = (int)floor(xh);
+        base[y * F + x] = iy * F + ix;
+        wy[y * F + x] = yh - iy;
+        wx[y * F + x] = xh - ix;
+        w[y * F + x] = make_float2((float)(yh - iy), (float)(xh - ix));
+      }
+    }
+  }
+  // exact transpose: entries grouped by model pixel, camera pixels in increasing order
+  std::vector<int32_t> count(FF + 1, 0);
+  for (int q = 0; q < FF; ++q) {
+    if (base[q] < 0) continue;
+    const int u = base[q];
+    count[u + 1]++; count[u + 2]++; count[u + F + 1]++; count[u + F + 2]++;
+  }
+  rt_ptr.assign(FF + 1, 0);
+  for (int u = 0; u < FF; ++u) rt_ptr[u + 1] = rt_ptr[u] + count[u + 1];
+  rt_idx.assign(rt_ptr[FF], 0);
+  rt_w.assign(rt_ptr[FF], 0.f);
+  std::vector<int32_t> fill(rt_ptr.begin(), rt_ptr.end() - 1);
+  for (int q = 0; q < FF; ++q) {
+    if (base[q] < 0) continue;
+    const int u = base[q];
+    const double v = wy[q], h = wx[q];
+    const int us[4] = {u, u + 1, u + F, u + F + 1};
+    const double ws[4] = {(1 - v) * (1 - h), (1 - v) * h, v * (1 - h), v * h};
+    for (int k = 0; k < 4; ++k) {
+      rt_idx[fill[us[k]]] = q;
+      rt_w[fill[us[k]]] = (float)ws[k];
+      fill[us[k]]++;
+    }
+  }
+}
+
+int check_device(const ptycho_plan* p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PTYCHO_ECUDA;
+  return dev == p->dev ? PTYCHO_OK : PTYCHO_EINVAL;
+}
+
+int dispatch(ptycho_plan* p, const CallArgs& c, cudaStream_t st) {
+  switch (p->F) {
+    case 64: return ptycho::run_pipeline<64>(*p, c, st);
+    case 128: return ptycho::run_pipeline<128>(*p, c, st);
+    case 256: return ptycho::run_pipeline<256>(*p, c, st);
+    case 512: return ptycho::run_pipeline<512>(*p, c, st);
+  }
+  return PTYCHO_EUNSUPPORTED;
+}
+
+int fill_batch(ptycho_plan* p, CallArgs& c, const int32_t* batch_idx, int nbatch) {
+  if (batch_idx) {
+    if (nbatch < 1 || nbatch > p->J) return PTYCHO_EINVAL;
+    c.bidx = batch_idx;
+    c.nbatch = nbatch;
+  } else {
+    c.bidx = p->d_ident;
+    c.nbatch = p->J;
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ptycho_strerror(int code) {
+  switch (code) {
+    case PTYCHO_OK: return "success";
+    case PTYCHO_EINVAL: return "invalid argument (shape, size, NULL pointer, option or device)";
+    case PTYCHO_ERANGE: return "a scan position puts a patch outside its object";
+    case PTYCHO_ENOMEM: return "device memory allocation failed";
+    case PTYCHO_ECUDA: return "a CUDA call or kernel launch failed";
+    case PTYCHO_ETIMEDOUT: return "a bounded device wait timed out";
+    case PTYCHO_EUNSUPPORTED: return "unsupported configuration (frame size or wavelength count)";
+  }
+  return "unknown error";
+}
+
+int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
+  if (!g || !out) return PTYCHO_EINVAL;
+  *out = nullptr;
+  if (g->L < 1 || g->M < 1 || g->J < 1 || !g->obj_h || !g->obj_w || !g->pos) return PTYCHO_EINVAL;
+  if (g->L > ptycho::kMaxL || !supported_F(g->F)) return PTYCHO_EUNSUPPORTED;
+  if (g->loss != PTYCHO_LOSS_AMPLITUDE && g->loss != PTYCHO_LOSS_POISSON) return PTYCHO_EINVAL;
+  if (!(g->eps >= 0.f) || !isfinite(g->eps)) return PTYCHO_EINVAL;
+  if (g->remap && !(g->z > 0.0 && g->det_pixel > 0.0 && isfinite(g->tilt_rad) && fabs(g->tilt_rad) < kPi / 2))
+    return PTYCHO_EINVAL;
+  const int F = g->F;
+  for (int l = 0; l < g->L; ++l)
+    if (g->obj_h[l] < F || g->obj_w[l] < F) return PTYCHO_EINVAL;
+  for (int l = 0; l < g->L; ++l)
+    for (int j = 0; j < g->J; ++j) {
+      const int y = g->pos[(l * g->J + j) * 2], x = g->pos[(l * g->J + j) * 2 + 1];
+      if (y < 0 || x < 0 || y > g->obj_h[l] - F || x > g->obj_w[l] - F) return PTYCHO_ERANGE;
+    }
+
+  ptycho_plan* p = new (std::nothrow) ptycho_plan();
+  if (!p) return PTYCHO_ENOMEM;
+  if (cudaGetDevice(&p->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess) {
+    delete p;
+    return PTYCHO_ECUDA;
+  }
+  p->L = g->L; p->M = g->M; p->F = F; p->J = g->J;
+  p->remap = g->remap ? 1 : 0;
+  p->loss_kind = g->loss;
+  p->eps = g->eps;
+  long long off = 0;
+  for (int l = 0; l < g->L; ++l) {
+    p->obj_h[l] = g->obj_h[l];
+    p->obj_w[l] = g->obj_w[l];
+    p->obj_off[l] = off;
+    off += (long long)g->obj_h[l] * g->obj_w[l];
+  }
+  p->O_numel = off;
+  p->P_numel = (long long)g->L * g->M * F * F;
+  p->pos_host.assign(g->pos, g->pos + (size_t)g->L * g->J * 2);
+
+  // batching: keep every mode's field of B positions in scratch when it fits the budget,
+  // otherwise one position at a time with the modes split into chunks (recomputed later).
+  const long long FF8 = (long long)F * F * (long long)sizeof(float2);
+  const long long LM = (long long)g->L * g->M;
+  p->scratch_budget = g->scratch_bytes > 0 ? g->scratch_bytes : kDefaultScratch;
+  if (LM * FF8 <= p->scratch_budget) {
+    p->store = 1;
+    p->C = (int)LM;
+    p->nchunks = 1;
+    p->B = (int)std::max<long long>(1, std::min<long long>(32, p->scratch_budget / (LM * FF8)));
+    p->B = std::min(p->B, g->J);
+  } else {
+    p->store = 0;
+    p->B = 1;
+    p->C = (int)std::max<long long>(1, std::min<long long>(LM, p->scratch_budget / FF8));
+    p->nchunks = (int)((LM + p->C - 1) / p->C);
+  }
+  int colblocks = 0;
+  switch (F) {
+    case 64: colblocks = F / ptycho::ColCfg<64>::W; break;
+    case 128: colblocks = F / ptycho::ColCfg<128>::W; break;
+    case 256: colblocks = F / ptycho::ColCfg<256>::W; break;
+    default: colblocks = F / ptycho::ColCfg<512>::W; break;
+  }
+  const long long target = 2ll * p->sms;
+  long long G = (target + (long long)colblocks * p->B - 1) / ((long long)colblocks * p->B);
+  G = std::max<long long>(1, std::min<long long>(G, p->C));
+  p->MG = (int)((p->C + G - 1) / G);
+  p->G = (p->C + p->MG - 1) / p->MG;
+
+  int rc = PTYCHO_OK;
+  const long long FF = (long long)F * F;
+  rc = rc ? rc : dalloc(p, &p->d_pos, (long long)g->L * g->J * 2);
+  rc = rc ? rc : dalloc(p, &p->d_ident, g->J);
+  rc = rc ? rc : dalloc(p, &p->d_tw, F);
+  rc = rc ? rc : dalloc(p, &p->d_S, (long long)p->B * p->C * FF);
+  rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->B * p->G * FF);
+  rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->B * FF);
+  rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / ptycho::kLossThreads));
+  rc = rc ? rc : dalloc(p, &p->d_gO, p->O_numel);
+  rc = rc ? rc : dalloc(p, &p->d_gP, p->P_numel);
+  rc = rc ? rc : dalloc(p, &p->d_status, 1);
+  if (!rc && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = PTYCHO_ECUDA;
+  if (rc) { free_plan(p); return rc; }
+
+  std::vector<int32_t> ident(g->J);
+  for (int j = 0; j < g->J; ++j) ident[j] = j;
+  // twiddles W_F^(t*k2) of the two-stage FFT, tw[t*N2 + k2], in FP64 then rounded
+  int N1 = 0, N2 = 0;
+  switch (F) {
+    case 64: N1 = ptycho::FftShape<64>::N1; N2 = ptycho::FftShape<64>::N2; break;
+    case 128: N1 = ptycho::FftShape<128>::N1; N2 = ptycho::FftShape<128>::N2; break;
+    case 256: N1 = ptycho::FftShape<256>::N1; N2 = ptycho::FftShape<256>::N2; break;
+    default: N1 = ptycho::FftShape<512>::N1; N2 = ptycho::FftShape<512>::N2; break;
+  }
+  std::vector<float2> tw((size_t)N1 * N2);
+  for (int t = 0; t < N1; ++t)
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const double ang = -2.0 * kPi * (double)((t * k2) % F) / (double)F;
+      tw[(size_t)t * N2 + k2] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+  rc = rc ? rc : upload(p->d_pos, p->pos_host.data(), (long long)p->pos_host.size());
+  rc = rc ? rc : upload(p->d_ident, ident.data(), g->J);
+  rc = rc ? rc : upload(p->d_tw, tw.data(), (long long)tw.size());
+  if (!rc && p->remap) {
+    std::vector<int32_t> base, rt_ptr, rt_idx;
+    std::vector<float2> w;
+    std::vector<float> rt_w;
+    build_remap(F, g->z, g->det_pixel, g->tilt_rad, base, w, rt_ptr, rt_idx, rt_w);
+    rc = rc ? rc : dalloc(p, &p->d_tap_base, FF);
+    rc = rc ? rc : dalloc(p, &p->d_tap_w, FF);
+    rc = rc ? rc : dalloc(p, &p->d_rt_ptr, FF + 1);
+    rc = rc ? rc : dalloc(p, &p->d_rt_idx, std::max<long long>(1, (long long)rt_idx.size()));
+    rc = rc ? rc : dalloc(p, &p->d_rt_w, std::max<long long>(1, (long long)rt_w.size()));
+    rc = rc ? rc : upload(p->d_tap_base, base.data(), FF);
+    rc = rc ? rc : upload(p->d_tap_w, w.data(), FF);
+    rc = rc ? rc : upload(p->d_rt_ptr, rt_ptr.data(), FF + 1);
+    rc = rc ? rc : upload(p->d_rt_idx, rt_idx.data(), (long long)rt_idx.size());
+    rc = rc ? rc : upload(p->d_rt_w, rt_w.data(), (long long)rt_w.size());
+  }
+  if (rc) { free_plan(p); return rc; }
+  *out = p;
+  return PTYCHO_OK;
+}
+
+int ptycho_plan_destroy(ptycho_plan_t* p) {
+  if (!p) return PTYCHO_OK;
+  cudaDeviceSynchronize();
+  free_plan(p);
+  return PTYCHO_OK;
+}
+
+int64_t ptycho_plan_workspace_bytes(const ptycho_plan_t* p) { return p ? p->bytes : 0; }
+int64_t ptycho_plan_numel_O(const ptycho_plan_t* p) { return p ? p->O_numel : 0; }
+int64_t ptycho_plan_numel_P(const ptycho_plan_t* p) { return p ? p->P_numel : 0; }
+int64_t ptycho_plan_last_launches(const ptycho_plan_t* p) { return p ? p->last_launches : 0; }
+
+int ptycho_plan_profile(ptycho_plan_t* p, int enable) {
+  if (!p) return PTYCHO_EINVAL;
+  p->prof = enable ? 1 : 0;
+  p->ev_used = 0;
+  p->ev_kind.clear();
+  return PTYCHO_OK;
+}
+
+int ptycho_plan_profile_read(ptycho_plan_t* p, double* ms, int64_t* launches) {
+  if (!p || !ms || !launches) return PTYCHO_EINVAL;
+  for (int k = 0; k < ptycho::kNumKinds; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  for (size_t i = 0; i < p->ev_used; ++i) {
+    if (cudaEventSynchronize(p->ev_pool[2 * i + 1]) != cudaSuccess) return PTYCHO_ECUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->ev_pool[2 * i], p->ev_pool[2 * i + 1]) != cudaSuccess) return PTYCHO_ECUDA;
+    ms[p->ev_kind[i]] += t;
+    launches[p->ev_kind[i]] += 1;
+  }
+  p->ev_used = 0;
+  p->ev_kind.clear();
+  return PTYCHO_OK;
+}
+
+const char* ptycho_kernel_name(int kind) {
+  static const char* names[] = {"row_fwd", "col_fwd", "loss", "col_adj", "row_adj", "obj_grad", "loss_reduce", "adam"};
+  return (kind >= 0 && kind < ptycho::kNumKinds) ? names[kind] : "unknown";
+}
+
+int ptycho_plan_status(ptycho_plan_t* p, int32_t* flags) {
+  if (!p || !flags) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  int v = 0;
+  if (cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PTYCHO_ECUDA;
+  if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return PTYCHO_ECUDA;
+  *flags = v;
+  return PTYCHO_OK;
+}
+
+int ptycho_forward(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
+                   float* I_pred, void* stream) {
+  if (!p || !O || !P || !I_pred) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  CallArgs c{};
+  c.kind = CallKind::Forward;
+  c.O = reinterpret_cast<const float2*>(O);
+  c.P = reinterpret_cast<const float2*>(P);
+  c.sigma = sigma;
+  c.bg = bg;
+  c.I_pred = I_pred;
+  fill_batch(p, c, nullptr, 0);
+  return dispatch(p, c, (cudaStream_t)stream);
+}
+
+int ptycho_loss(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
+                const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
+                int nbatch, double* loss_dev, void* stream) {
+  if (!p || !O || !P || !I_meas || !loss_dev) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  CallArgs c{};
+  c.kind = CallKind::Loss;
+  c.O = reinterpret_cast<const float2*>(O);
+  c.P = reinterpret_cast<const float2*>(P);
+  c.sigma = sigma;
+  c.bg = bg;
+  c.Imeas = I_meas;
+  c.mask = mask;
+  c.mask_per_frame = mask_per_frame ? 1 : 0;
+  c.loss = loss_dev;
+  rc = fill_batch(p, c, batch_idx, nbatch);
+  if (rc) return rc;
+  return dispatch(p, c, (cudaStream_t)stream);
+}
+
+int ptycho_adjoint(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
+                   const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
+                   int nbatch, float* gO, float* gP, double* loss_dev, void* stream) {
+  if (!p || !O || !P || !I_meas || !gO || !gP) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  CallArgs c{};
+  c.kind = CallKind::Adjoint;
+  c.O = reinterpret_cast<const float2*>(O);
+  c.P = reinterpret_cast<const float2*>(P);
+  c.sigma = sigma;
+  c.bg = bg;
+  c.Imeas = I_meas;
+  c.mask = mask;
+  c.mask_per_frame = mask_per_frame ? 1 : 0;
+  c.gO = reinterpret_cast<float2*>(gO);
+  c.gP = reinterpret_cast<float2*>(gP);
+  c.loss = loss_dev;
+  rc = fill_batch(p, c, batch_idx, nbatch);
+  if (rc) return rc;
+  return dispatch(p, c, (cudaStream_t)stream);
+}
+
+int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, const float* sigma, const float* bg,
+                const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
+                int nbatch, double* loss_dev, void* stream) {
+  if (!p || !s || !O || !P || !I_meas || !s->mO || !s->vO || !s->mP || !s->vP) return PTYCHO_EINVAL;
+  if (!(s->beta1 >= 0.f && s->beta1 < 1.f && s->beta2 >= 0.f && s->beta2 < 1.f && s->eps >= 0.f)) return PTYCHO_EINVAL;
+  int rc = ptycho_adjoint(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
+                          reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP), loss_dev, stream);
+  if (rc) return rc;
+  s->t += 1;
+  const double c1 = 1.0 / (1.0 - pow((double)s->beta1, (double)s->t));
+  const double c2 = 1.0 / (1.0 - pow((double)s->beta2, (double)s->t));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;
+  const int grid = 4 * p->sms;
+  long long ev = ptycho::prof_begin(*p, ptycho::kAdam, st);
+  ptycho::k_adam<<<grid, 256, 0, st>>>(O, reinterpret_cast<const float*>(p->d_gO), s->mO, s->vO, nO, s->lr_O,
+                                       s->beta1, s->beta2, s->eps, (float)c1, (float)c2);
+  ++p->last_launches;
+  if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
+  ptycho::prof_end(*p, ev, st);
+  ev = ptycho::prof_begin(*p, ptycho::kAdam, st);
+  ptycho::k_adam<<<grid, 256, 0, st>>>(P, reinterpret_cast<const float*>(p->d_gP), s->mP, s->vP, nP, s->lr_P,
+                                       s->beta1, s->beta2, s->eps, (float)c1, (float)c2);
+  ++p->last_launches;
+  if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
+  ptycho::prof_end(*p, ev, st);
+  return PTYCHO_OK;
+}
+
+}  // extern "C"

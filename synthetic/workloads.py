@@ -28,7 +28,8 @@ __all__ = [
     "Geometry", "Workload", "smooth_noise", "zernike_noll", "zernike_phase",
     "gaussian_amplitude", "probe_modes", "elliptical_aperture_modes",
     "object_smooth", "object_rectangles", "raster_positions", "scale_positions",
-    "round_half_away", "poisson_measure", "default_eps", "config1", "config2",
+    "round_half_away", "poisson_measure", "default_eps", "config1", "config2", "near_truth",
+    "serving_workload",
     "config3", "config4", "config5_requests", "tiny_workload", "CONFIG3_GRID",
 ]
 
@@ -395,6 +396,23 @@ def serving_workload(desc: dict) -> Workload:
     w.P0 = P0
     w.name = f"request{desc['index']}_F{F}_J{J}_L{L}_M{M}"
     return w
+
+
+def near_truth(w: Workload, seed: int = 0, amp: float = 0.05):
+    """An evaluation point close to the ground truth: small smooth amplitude and phase
+    perturbations of every object and a small extra Zernike phase on every probe mode."""
+    rng = np.random.default_rng(seed)
+    O = []
+    for o in w.O_true:
+        s1 = smooth_noise(rng, o.shape, 4.0) - 0.5
+        s2 = smooth_noise(rng, o.shape, 4.0) - 0.5
+        O.append(o * (1.0 + amp * s1) * np.exp(1j * amp * s2))
+    P = np.empty_like(w.P_true)
+    for l in range(w.L):
+        for m in range(w.M):
+            c = rng.normal(0.0, amp, size=10)
+            P[l, m] = w.P_true[l, m] * np.exp(1j * zernike_phase(w.F, c, w.F / 2))
+    return O, P
 
 
 def tiny_workload(F: int = 16, L: int = 2, M: int = 2, n_side: int = 3, step: int = 4,

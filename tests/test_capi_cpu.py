@@ -1,0 +1,107 @@
+"""Boundary checks that need no GPU: the library builds, loads, exports every symbol that
+``include/ptycho.h`` declares, and rejects bad arguments on the host before any launch."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptycho.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_14780_gb300 import _native, build
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    return _native.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptycho_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = declared_symbols()
+    for must in ("ptycho_plan_create", "ptycho_plan_destroy", "ptycho_forward", "ptycho_loss",
+                 "ptycho_adjoint", "ptycho_step", "ptycho_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(lib._name)
+    for name in declared_symbols():
+        assert hasattr(raw, name), name
+
+
+def test_binding_declares_every_exported_symbol():
+    from paper_2311_14780_gb300 import _native
+    bound = {s[0] for s in _native.SIGNATURES}
+    assert set(declared_symbols()) <= bound | {"ptycho_plan_create"}
+
+
+def test_strerror(lib):
+    assert lib.ptycho_strerror(0) == b"success"
+    assert b"outside" in lib.ptycho_strerror(-2)
+    assert lib.ptycho_strerror(-99) == b"unknown error"
+
+
+def _geom(F=64, L=1, M=1, J=2, H=80, W=80, pos=None, loss=0, remap=0, tilt=1.2):
+    from paper_2311_14780_gb300 import _native
+    g = _native.Geom()
+    keep = {}
+    keep["h"] = np.full(L, H, np.int32)
+    keep["w"] = np.full(L, W, np.int32)
+    keep["pos"] = np.zeros((L, J, 2), np.int32) if pos is None else np.ascontiguousarray(pos, np.int32)
+    g.L, g.M, g.F, g.J = L, M, F, J
+    g.obj_h = keep["h"].ctypes.data_as(_native.c_int32_p)
+    g.obj_w = keep["w"].ctypes.data_as(_native.c_int32_p)
+    g.pos = keep["pos"].ctypes.data_as(_native.c_int32_p)
+    g.z, g.det_pixel, g.tilt_rad = 0.088, 15e-6, tilt
+    g.remap, g.loss, g.eps = remap, loss, 0.0
+    return g, keep
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(F=100), -6),            # frame size not supported
+    (dict(L=17, J=1), -6),        # more wavelengths than the ABI supports
+    (dict(L=0), -1),
+    (dict(M=0), -1),
+    (dict(J=0), -1),
+    (dict(loss=7), -1),
+    (dict(H=32), -1),             # object smaller than a frame
+    (dict(remap=1, tilt=2.0), -1),
+])
+def test_plan_create_rejects_bad_geometry_on_the_host(lib, kw, code):
+    g, keep = _geom(**kw)
+    h = ctypes.c_void_p()
+    assert lib.ptycho_plan_create(ctypes.byref(g), ctypes.byref(h)) == code
+    assert not h.value
+
+
+@pytest.mark.parametrize("bad", [(17, 0), (0, 17), (-1, 0), (0, -1)])
+def test_plan_create_rejects_patches_outside_the_object(lib, bad):
+    pos = np.zeros((1, 2, 2), np.int32)
+    pos[0, 1] = bad
+    g, keep = _geom(pos=pos)
+    h = ctypes.c_void_p()
+    assert lib.ptycho_plan_create(ctypes.byref(g), ctypes.byref(h)) == -2
+
+
+def test_null_arguments_are_rejected(lib):
+    h = ctypes.c_void_p()
+    assert lib.ptycho_plan_create(None, ctypes.byref(h)) == -1
+    assert lib.ptycho_forward(None, None, None, None, None, None, None) == -1
+    assert lib.ptycho_plan_destroy(None) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2311_14780_gb300 import _native
+    monkeypatch.setattr(_native, "_LIB", None)
+    monkeypatch.setattr(_native, "lib_path", lambda: str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _native.lib()
