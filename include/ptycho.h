@@ -47,6 +47,7 @@ extern "C" {
 #define PTYCHO_ECUDA (-4)        /* a CUDA call or kernel launch failed                */
 #define PTYCHO_ETIMEDOUT (-5)    /* a bounded device wait ran out (serving loop)       */
 #define PTYCHO_EUNSUPPORTED (-6) /* frame size not in {64, 128, 256, 512}, L > 16      */
+#define PTYCHO_ETOOLARGE (-7)    /* problem does not fit ptycho_forward_noalloc's array */
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */
@@ -162,6 +163,30 @@ int ptycho_plan_status(ptycho_plan_t* plan, int32_t* flags);
 int ptycho_plan_profile(ptycho_plan_t* plan, int enable);
 int ptycho_plan_profile_read(ptycho_plan_t* plan, double* ms, int64_t* launches);
 const char* ptycho_kernel_name(int kind);
+
+/* Allocation-free forward model.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc while they run (an application that gives all
+ * device memory to its own pool at start-up, a latency-critical loop that cannot take the
+ * synchronisation an allocation may cause, a deployment that bans allocation after
+ * initialisation).  It computes exactly what ptycho_forward computes for a plan without
+ * the tilted-plane remap, but needs no plan: every intermediate lives in one fixed device
+ * array of PTYCHO_NOALLOC_SCRATCH_BYTES (32 MiB) that each GPU loading this library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   L, M, F, J, obj_h, obj_w  as in ptycho_geom_t (HOST arrays)
+ *   pos     HOST [L][J][2] scan positions, validated like ptycho_plan_create (PTYCHO_ERANGE)
+ *   O, P, sigma, bg, I_pred  DEVICE arrays as in ptycho_forward
+ * Returns PTYCHO_ETOOLARGE when the position tables plus one complex and one real frame
+ * exceed the fixed array; larger mode counts are processed in chunks that fit.
+ * Set-up: the first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  The small host tables
+ * are copied with cudaMemcpyAsync from pageable memory, so the call waits for the stream's
+ * earlier work before it returns.  All calls share the one array and it keeps the previous
+ * call's contents: calls whose work overlaps on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
+#define PTYCHO_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J, const int32_t* obj_h,
+                           const int32_t* obj_w, const int32_t* pos, const float* O, const float* P,
+                           const float* sigma, const float* bg, float* I_pred, void* stream);
 
 /* Static text for a return code. */
 const char* ptycho_strerror(int code);

@@ -51,6 +51,8 @@ SIGNATURES = [
     ("ptycho_plan_profile", _I, [_VP, _I]),
     ("ptycho_plan_profile_read", _I, [_VP, c_double_p, ctypes.POINTER(ctypes.c_int64)]),
     ("ptycho_kernel_name", ctypes.c_char_p, [_I]),
+    ("ptycho_forward_noalloc", _I, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_int32_p,
+                                    c_int32_p, c_int32_p, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 

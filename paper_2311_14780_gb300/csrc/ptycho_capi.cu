@@ -199,6 +199,7 @@ const char* ptycho_strerror(int code) {
     case PTYCHO_ECUDA: return "a CUDA call or kernel launch failed";
     case PTYCHO_ETIMEDOUT: return "a bounded device wait timed out";
     case PTYCHO_EUNSUPPORTED: return "unsupported configuration (frame size or wavelength count)";
+    case PTYCHO_ETOOLARGE: return "problem does not fit the fixed array of the allocation-free entry point";
   }
   return "unknown error";
 }
