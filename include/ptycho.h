@@ -159,7 +159,8 @@ int ptycho_plan_status(ptycho_plan_t* plan, int32_t* flags);
 #define PTYCHO_K_OBJ_GRAD 5      /* tile-owned object-gradient sum                        */
 #define PTYCHO_K_LOSS_REDUCE 6   /* FP64 loss reduction                                   */
 #define PTYCHO_K_ADAM 7          /* Adam update                                          */
-#define PTYCHO_NUM_KERNELS 8
+#define PTYCHO_K_REMAP_ADJ 8     /* R^T of the tilted-plane remap                         */
+#define PTYCHO_NUM_KERNELS 9
 int ptycho_plan_profile(ptycho_plan_t* plan, int enable);
 int ptycho_plan_profile_read(ptycho_plan_t* plan, double* ms, int64_t* launches);
 const char* ptycho_kernel_name(int kind);

@@ -56,7 +56,7 @@ SIGNATURES = [
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 
-NUM_KERNELS = 8
+NUM_KERNELS = 9
 _LIB = None
 
 

@@ -6,13 +6,14 @@
 // every exit wave goes through a scratch buffer S[B][C][F][F] (complex64) sized to stay in
 // the GPU's L2 cache:
 //
-//   k_row_fwd   psi = sigma_j P_lm * O_l(r - s_j) for one row; 1D FFT along the row -> S
+//   k_row_fwd   psi = sigma_j P_lm * O_l(r - s_j) for one row of every mode of a wavelength
+//               (the object row is read once); 1D FFT along the row -> S
 //   k_col_fwd   1D FFT along columns of S -> Psi (scaled by 1/F); accumulate |Psi|^2 over
 //               the modes of a group into Ipart; optionally keep Psi in S for the adjoint
 //   k_loss      I = sum of groups (+ background) on the model grid; tilted-plane remap to the
 //               camera grid; mask; loss terms (FP64 block partials) and D = mask dL/dI
-//   k_col_adj   G = R^T D on the model grid; Psi (kept, or recomputed from S);
-//               (2/F) G Psi; inverse 1D FFT along columns -> S
+//   k_remap_adj G = R^T D on the model grid (only with the remap; otherwise G = D)
+//   k_col_adj   Psi (kept, or recomputed from S); (2/F) G Psi; inverse column DFT -> S
 //   k_row_adj   inverse 1D FFT along rows -> chi = dL/dpsi; grad P_lm += conj(sigma p) chi
 //               summed over the batch in registers; S <- conj(sigma P_lm) chi
 //   k_obj_grad  grad O_l tile += sum over the batch's overlapping patches and the chunk's
@@ -27,6 +28,7 @@ namespace ptycho {
 constexpr int kMaxL = 16;
 constexpr int kLossThreads = 256;
 constexpr int kTile = 32;        // object-gradient tile side
+constexpr int kMaxB = 32;        // positions per batch (upper bound)
 
 struct KArgs {
   int L, M, F, J;
@@ -36,7 +38,7 @@ struct KArgs {
   const int32_t* bidx;           // positions of this call, in processing order
   int nbatch;                    // number of entries in bidx
   int batch_off;                 // first entry of the current position batch
-  int nb;                        // positions in the current batch (<= B)
+  int nb;                        // positions in the current batch (<= B <= kMaxB)
   const float* sigma;            // [J] power coefficients or null
   const float2* tw;              // W_F^(t*k2) table
   int C;                         // stride (modes) of the scratch buffer
@@ -44,6 +46,8 @@ struct KArgs {
   int MG;                        // modes per column-kernel group
   int G;                         // groups per chunk (Ipart has G slices per position)
   int* status;                   // device status word (bit 0: a position index was out of range)
+  int box[kMaxL][4];             // per wavelength: rows [box0, box2) x cols [box1, box3) covered by
+                                 // the batch's patches (the whole object when not known on the host)
 };
 
 // Position index of batch entry i, or -1 (and the status bit set) if out of range.
@@ -54,6 +58,23 @@ __device__ __forceinline__ int batch_pos(const KArgs& a, int i) {
     return -1;
   }
   return j;
+}
+
+// Scan positions (row, col) of the current batch for wavelength l and their power
+// coefficients, staged in shared memory by the first nb threads; invalid entries become
+// (-1, -1).  Ends with a block barrier.
+__device__ __forceinline__ void stage_batch(const KArgs& a, int l, int2* spos, float* ssig) {
+  if ((int)threadIdx.x < a.nb) {
+    const int j = batch_pos(a, a.batch_off + threadIdx.x);
+    if (j < 0) {
+      spos[threadIdx.x] = make_int2(-1, -1);
+      ssig[threadIdx.x] = 0.f;
+    } else {
+      spos[threadIdx.x] = make_int2(a.pos[(l * a.J + j) * 2], a.pos[(l * a.J + j) * 2 + 1]);
+      ssig[threadIdx.x] = a.sigma ? __ldg(a.sigma + j) : 1.0f;
+    }
+  }
+  __syncthreads();
 }
 
 template <int F> struct RowCfg {
@@ -72,8 +93,8 @@ template <int F> struct ColCfg {
 __device__ __forceinline__ float sigma_of(const KArgs& a, int j) { return a.sigma ? __ldg(a.sigma + j) : 1.0f; }
 
 // ---------------------------------------------------------------------------------------
-// forward row pass: exit wave (f1, f2, f3) and the row DFT (first half of f4)
-// grid (F/RPB, chunk_len, nb)
+// forward row pass: exit waves (f1, f2, f3) of every mode of wavelength l in the chunk and
+// the row DFT (first half of f4).   grid (F/RPB, L, nb)
 // ---------------------------------------------------------------------------------------
 template <int F>
 __global__ void __launch_bounds__(RowCfg<F>::threads)
@@ -82,25 +103,27 @@ k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   extern __shared__ float2 smem[];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
   const int r = blockIdx.x * RowCfg<F>::RPB + vec;
-  const int cm = blockIdx.y, b = blockIdx.z;
-  const int mode = a.chunk_base + cm;
-  const int l = mode / a.M;
+  const int l = blockIdx.y, b = blockIdx.z;
+  const int mlo = max(a.chunk_base, l * a.M), mhi = min(a.chunk_base + a.chunk_len, (l + 1) * a.M);
+  if (mlo >= mhi) return;                             // uniform over the block
   const int j = batch_pos(a, a.batch_off + b);
   if (j < 0) return;                                  // uniform over the block
   const int y = a.pos[(l * a.J + j) * 2], x = a.pos[(l * a.J + j) * 2 + 1];
   const float s = sigma_of(a, j);
   const float2* Orow = O + a.obj_off[l] + (long long)(y + r) * a.obj_w[l] + x;
-  const float2* Prow = P + ((long long)mode * F + r) * F;
-  float2 v[N2];
+  float2 p[N2];
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) {
-    const int c = t + N1 * n2;
-    v[n2] = cscale(cmul(__ldg(Prow + c), __ldg(Orow + c)), s);
+  for (int n2 = 0; n2 < N2; ++n2) p[n2] = cscale(__ldg(Orow + t + N1 * n2), s);
+  for (int mode = mlo; mode < mhi; ++mode) {
+    const float2* Prow = P + ((long long)mode * F + r) * F;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = cmul(__ldg(Prow + t + N1 * n2), p[n2]);
+    fft_fwd_I2O<F>(v, t, smem + vec * Xch<F>::region_rows, a.tw, WarpSync{});
+    float2* out = S + (((long long)b * a.C + (mode - a.chunk_base)) * F + r) * F;
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) out[idxO<F>(t, sl)] = v[sl];
   }
-  fft_fwd_I2O<F>(v, t, smem + vec * Xch<F>::region_rows, a.tw, WarpSync{});
-  float2* out = S + (((long long)b * a.C + cm) * F + r) * F;
-#pragma unroll
-  for (int sl = 0; sl < N2; ++sl) out[idxO<F>(t, sl)] = v[sl];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -144,8 +167,9 @@ k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_
 }
 
 // ---------------------------------------------------------------------------------------
-// measurement (f5) and loss: camera-grid prediction, masked loss partials, D = mask dL/dI
-// grid (F*F/256, nb)
+// measurement (f5) and loss: camera-grid prediction, masked loss partials, D = mask dL/dI.
+// One thread per camera pixel, looping over the batch (the remap taps are read once).
+// grid (F*F/256)
 // ---------------------------------------------------------------------------------------
 struct LossArgs {
   const float* Ipart;            // [B][G][F][F] model grid (centred)
@@ -193,76 +217,99 @@ __global__ void __launch_bounds__(kLossThreads)
 k_loss(KArgs a, LossArgs la) {
   constexpr int FF = F * F;
   __shared__ double red[kLossThreads / 32];
-  const int b = blockIdx.y;
-  const int i = a.batch_off + b;
-  const int j = batch_pos(a, i);
-  if (j < 0) {                                        // uniform over the block
-    if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = 0.0;
-    if (la.D) la.D[(long long)b * FF + blockIdx.x * kLossThreads + threadIdx.x] = 0.f;
-    return;
-  }
   const int q = blockIdx.x * kLossThreads + threadIdx.x;
-  const float* Ip = la.Ipart + (long long)b * a.G * FF;
-  float Ic = 0.f;
+  int u = q;
+  float2 w = make_float2(0.f, 0.f);
   bool valid = true;
   if (la.remap) {
-    const int u = la.tap_base[q];
-    if (u < 0) {
-      valid = false;
-    } else {
-      const float2 w = la.tap_w[q];
-      const float i00 = model_I(Ip, la.bg, a.G, FF, u), i01 = model_I(Ip, la.bg, a.G, FF, u + 1);
-      const float i10 = model_I(Ip, la.bg, a.G, FF, u + F), i11 = model_I(Ip, la.bg, a.G, FF, u + F + 1);
-      Ic = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
-    }
-  } else {
-    Ic = model_I(Ip, la.bg, a.G, FF, q);
+    u = la.tap_base[q];
+    valid = u >= 0;
+    if (valid) w = la.tap_w[q];
   }
-  if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
-  double term = 0.0;
-  if (la.D || la.loss_part) {
-    bool use = valid;
-    if (la.mask) use = use && (la.mask[(la.mask_per_frame ? (long long)j * FF : 0) + q] != 0);
-    float d = 0.f;
-    if (use) {
-      const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
-      const float Ie = Ic + la.eps;
-      if (la.loss_kind == 0) {
-        const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
-        term = (double)(diff * diff);
-        d = diff / se;
-      } else {
-        term = (double)poisson_term(Ie, Ih);
-        d = (Ie - Ih) / Ie;
+  const bool mask_shared = (la.mask && !la.mask_per_frame) ? (la.mask[q] != 0) : true;
+  for (int b = 0; b < a.nb; ++b) {
+    const int i = a.batch_off + b;
+    const int j = batch_pos(a, i);                   // uniform over the block
+    double term = 0.0;
+    if (j >= 0) {
+      const float* Ip = la.Ipart + (long long)b * a.G * FF;
+      float Ic = 0.f;
+      if (valid) {
+        if (la.remap) {
+          const float i00 = model_I(Ip, la.bg, a.G, FF, u), i01 = model_I(Ip, la.bg, a.G, FF, u + 1);
+          const float i10 = model_I(Ip, la.bg, a.G, FF, u + F), i11 = model_I(Ip, la.bg, a.G, FF, u + F + 1);
+          Ic = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
+        } else {
+          Ic = model_I(Ip, la.bg, a.G, FF, q);
+        }
       }
+      if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
+      if (la.D || la.loss_part) {
+        bool use = valid && mask_shared;
+        if (la.mask && la.mask_per_frame) use = use && (la.mask[(long long)j * FF + q] != 0);
+        float d = 0.f;
+        if (use) {
+          const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
+          const float Ie = Ic + la.eps;
+          if (la.loss_kind == 0) {
+            const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
+            term = (double)(diff * diff);
+            d = diff / se;
+          } else {
+            term = (double)poisson_term(Ie, Ih);
+            d = (Ie - Ih) / Ie;
+          }
+        }
+        if (la.D) la.D[(long long)b * FF + q] = d;
+      }
+    } else if (la.D) {
+      la.D[(long long)b * FF + q] = 0.f;
     }
-    if (la.D) la.D[(long long)b * FF + q] = d;
-  }
-  if (la.loss_part) {
+    if (la.loss_part) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < kLossThreads / 32; ++w) s += red[w];
-      la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = s;
+      for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int wi = 0; wi < kLossThreads / 32; ++wi) s += red[wi];
+        la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = s;
+      }
+      __syncthreads();
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// adjoint column pass: G = R^T D, (2/F) G Psi, inverse column DFT
-// grid (F/W, G, nb)
+// R^T of the tilted-plane remap: G[b][u] = sum over the camera pixels q that sample model
+// pixel u of w_uq D[b][q] (CSR rows in increasing q: a fixed order).   grid (F*F/256)
 // ---------------------------------------------------------------------------------------
 struct AdjArgs {
   const float* D;                // [B][F][F] camera grid
   const int32_t* rt_ptr;         // [F*F+1] CSR of R^T over centred model pixels (remap only)
   const int32_t* rt_idx;         // camera pixel of each entry
   const float* rt_w;             // weight of each entry
+  float* Gt;                     // [B][F][F] R^T D on the model grid (remap only)
   int remap;
 };
 
+template <int F>
+__global__ void __launch_bounds__(256)
+k_remap_adj(KArgs a, AdjArgs aa) {
+  constexpr int FF = F * F;
+  const int u = blockIdx.x * 256 + threadIdx.x;
+  const int e0 = __ldg(aa.rt_ptr + u), e1 = __ldg(aa.rt_ptr + u + 1);
+  for (int b = 0; b < a.nb; ++b) {
+    const float* Db = aa.D + (long long)b * FF;
+    float gv = 0.f;
+    for (int e = e0; e < e1; ++e) gv = fmaf(__ldg(aa.rt_w + e), Db[__ldg(aa.rt_idx + e)], gv);
+    aa.Gt[(long long)b * FF + u] = gv;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint column pass: (2/F) G Psi, inverse column DFT.   grid (F/W, G, nb)
+// ---------------------------------------------------------------------------------------
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
 k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
@@ -272,20 +319,12 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
   const int c = threadIdx.x % W, t = threadIdx.x / W;
   const int col0 = blockIdx.x * W;
   const int g = blockIdx.y, b = blockIdx.z;
-  const float* Db = aa.D + (long long)b * F * F;
+  const float* Gb = (aa.remap ? aa.Gt : aa.D) + (long long)b * F * F;
   const float scale = 2.0f / (float)F;
   for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
     const int k = e / W, ce = e % W;
     const int u = ((k + F / 2) & (F - 1)) * F + ((col0 + ce + F / 2) & (F - 1));
-    float gv;
-    if (aa.remap) {
-      gv = 0.f;
-      const int e1 = __ldg(aa.rt_ptr + u + 1);
-      for (int q = __ldg(aa.rt_ptr + u); q < e1; ++q) gv = fmaf(__ldg(aa.rt_w + q), Db[__ldg(aa.rt_idx + q)], gv);
-    } else {
-      gv = Db[u];
-    }
-    gt[k * W + ce] = gv * scale;
+    gt[k * W + ce] = Gb[u] * scale;
   }
   __syncthreads();
   const int col = col0 + c;
@@ -322,35 +361,41 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
           float2* __restrict__ gP, KArgs a) {
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowCfg<F>::T;
   extern __shared__ float2 smem[];
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
   const int r = blockIdx.x * RowCfg<F>::RPB + vec;
   const int cm = blockIdx.y;
   const int mode = a.chunk_base + cm;
   const int l = mode / a.M;
+  stage_batch(a, l, spos, ssig);
   const float2* Prow = P + ((long long)mode * F + r) * F;
-  float2 acc[N2];
+  const float2* Ol = O + a.obj_off[l];
+  const int Wl = a.obj_w[l];
+  float2 pr[N2], acc[N2];
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) acc[n2] = make_float2(0.f, 0.f);
+  for (int n2 = 0; n2 < N2; ++n2) {
+    pr[n2] = __ldg(Prow + t + N1 * n2);
+    acc[n2] = make_float2(0.f, 0.f);
+  }
   for (int b = 0; b < a.nb; ++b) {
-    const int j = batch_pos(a, a.batch_off + b);
-    if (j < 0) continue;                              // uniform over the block
-    const int y = a.pos[(l * a.J + j) * 2], x = a.pos[(l * a.J + j) * 2 + 1];
-    const float s = sigma_of(a, j);
+    const int2 yx = spos[b];
+    if (yx.x < 0) continue;                           // uniform over the block
+    const float s = ssig[b];
     float2* row = S + (((long long)b * a.C + cm) * F + r) * F;
-    float2 v[N2];
+    const float2* Orow = Ol + (long long)(yx.x + r) * Wl + yx.y;
+    float2 v[N2], p[N2];
 #pragma unroll
     for (int sl = 0; sl < N2; ++sl) v[sl] = row[idxO<F>(t, sl)];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) p[n2] = __ldg(Orow + t + N1 * n2);
     fft_inv_O2I<F>(v, t, smem + vec * Xch<F>::region_rows, a.tw, WarpSync{});
-    const float2* Orow = O + a.obj_off[l] + (long long)(y + r) * a.obj_w[l] + x;
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) {
-      const int c = t + N1 * n2;
-      const float2 p = __ldg(Orow + c);
-      const float2 pr = __ldg(Prow + c);
-      const float2 gp = cconjmul(p, v[n2]);        // conj(p) chi
+      const float2 gp = cconjmul(p[n2], v[n2]);     // conj(p) chi
       acc[n2].x = fmaf(s, gp.x, acc[n2].x);
       acc[n2].y = fmaf(s, gp.y, acc[n2].y);
-      row[c] = cscale(cconjmul(pr, v[n2]), s);     // conj(sigma P) chi
+      row[t + N1 * n2] = cscale(cconjmul(pr[n2], v[n2]), s);     // conj(sigma P) chi
     }
   }
   float2* g = gP + ((long long)mode * F + r) * F;
@@ -362,68 +407,59 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
 }
 
 // ---------------------------------------------------------------------------------------
-// object gradient: each block owns 32x32 tiles of grad O_l inside the batch's bounding box
-// and adds, in a fixed order, every overlapping patch contribution of the chunk's modes.
-// grid (nblocks, L)
+// object gradient: one block per 32x32 tile of grad O_l inside the batch's bounding box; it
+// adds, in a fixed order, every overlapping patch contribution of the chunk's modes.
+// grid (tiles of the largest box, L)
 // ---------------------------------------------------------------------------------------
 template <int F>
 __global__ void __launch_bounds__(256)
 k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
   const int l = blockIdx.y;
   const int mlo = max(a.chunk_base, l * a.M), mhi = min(a.chunk_base + a.chunk_len, (l + 1) * a.M);
-  if (mlo >= mhi) return;
-  __shared__ int box[4];
-  if (threadIdx.x == 0) {
-    int y0 = 1 << 30, x0 = 1 << 30, y1 = -1, x1 = -1;
-    for (int b = 0; b < a.nb; ++b) {
-      const int j = batch_pos(a, a.batch_off + b);
-      if (j < 0) continue;
-      const int y = a.pos[(l * a.J + j) * 2], x = a.pos[(l * a.J + j) * 2 + 1];
-      y0 = min(y0, y); x0 = min(x0, x); y1 = max(y1, y + F); x1 = max(x1, x + F);
-    }
-    if (y1 < 0) { y0 = 0; x0 = 0; y1 = 0; x1 = 0; }   // no valid position: empty box
-    box[0] = y0; box[1] = x0; box[2] = y1; box[3] = x1;
-  }
-  __syncthreads();
-  const int by0 = box[0], bx0 = box[1];
-  const int nty = (box[2] - by0 + kTile - 1) / kTile, ntx = (box[3] - bx0 + kTile - 1) / kTile;
+  if (mlo >= mhi) return;                             // uniform over the block
+  const int by0 = a.box[l][0], bx0 = a.box[l][1];
+  const int ntx = (a.box[l][3] - bx0 + kTile - 1) / kTile;
+  const int nty = (a.box[l][2] - by0 + kTile - 1) / kTile;
+  if ((int)blockIdx.x >= ntx * nty) return;          // uniform over the block
+  stage_batch(a, l, spos, ssig);
+  const int oy0 = by0 + ((int)blockIdx.x / ntx) * kTile, ox0 = bx0 + ((int)blockIdx.x % ntx) * kTile;
   const int H = a.obj_h[l], Wd = a.obj_w[l];
-  float2* g = gO + a.obj_off[l];
   const int tx = threadIdx.x % kTile, ty0 = threadIdx.x / kTile;   // 8 row slots
-  for (int tile = blockIdx.x; tile < nty * ntx; tile += gridDim.x) {
-    const int oy0 = by0 + (tile / ntx) * kTile, ox0 = bx0 + (tile % ntx) * kTile;
-    const int ox = ox0 + tx;
-    float2 acc[kTile / 8];
+  const int ox = ox0 + tx;
+  float2 acc[kTile / 8];
 #pragma unroll
-    for (int k = 0; k < kTile / 8; ++k) acc[k] = make_float2(0.f, 0.f);
-    for (int b = 0; b < a.nb; ++b) {
-      const int j = a.bidx[a.batch_off + b];
-      if (j < 0 || j >= a.J) continue;
-      const int y = a.pos[(l * a.J + j) * 2], x = a.pos[(l * a.J + j) * 2 + 1];
-      if (y >= oy0 + kTile || y + F <= oy0 || x >= ox0 + kTile || x + F <= ox0) continue;
-      const bool in_x = ox >= x && ox < x + F;
-      for (int mode = mlo; mode < mhi; ++mode) {
-        const float2* src = S + ((long long)b * a.C + (mode - a.chunk_base)) * F * F;
+  for (int k = 0; k < kTile / 8; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int b = 0; b < a.nb; ++b) {
+    const int y = spos[b].x, x = spos[b].y;
+    if (y < 0 || y >= oy0 + kTile || y + F <= oy0 || x >= ox0 + kTile || x + F <= ox0) continue;
+    const bool in_x = ox >= x && ox < x + F;
+    const float2* src = S + ((long long)b * a.C + (mlo - a.chunk_base)) * F * F + (ox - x);
+    for (int mode = mlo; mode < mhi; ++mode, src += (long long)F * F) {
+      float2 v[kTile / 8];
 #pragma unroll
-        for (int k = 0; k < kTile / 8; ++k) {
-          const int oy = oy0 + ty0 + 8 * k;
-          if (in_x && oy >= y && oy < y + F) acc[k] = cadd(acc[k], src[(long long)(oy - y) * F + (ox - x)]);
-        }
+      for (int k = 0; k < kTile / 8; ++k) {
+        const int oy = oy0 + ty0 + 8 * k;
+        v[k] = (in_x && oy >= y && oy < y + F) ? src[(long long)(oy - y) * F] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int k = 0; k < kTile / 8; ++k) acc[k] = cadd(acc[k], v[k]);
     }
+  }
+  float2* g = gO + a.obj_off[l];
 #pragma unroll
-    for (int k = 0; k < kTile / 8; ++k) {
-      const int oy = oy0 + ty0 + 8 * k;
-      if (oy < H && ox < Wd) {
-        float2* p = g + (long long)oy * Wd + ox;
-        *p = cadd(*p, acc[k]);
-      }
+  for (int k = 0; k < kTile / 8; ++k) {
+    const int oy = oy0 + ty0 + 8 * k;
+    if (oy < H && ox < Wd) {
+      float2* p = g + (long long)oy * Wd + ox;
+      *p = cadd(*p, acc[k]);
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// loss reduction and Adam
+// loss reduction and Adam (defined in ptycho_capi.cu)
 // ---------------------------------------------------------------------------------------
 __global__ void k_loss_reduce(const double* __restrict__ part, long long n, double* out);
 __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m,

@@ -75,7 +75,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   aa.rt_ptr = p.d_rt_ptr;
   aa.rt_idx = p.d_rt_idx;
   aa.rt_w = p.d_rt_w;
+  aa.Gt = p.d_Gt;
   aa.remap = p.remap;
+  // batches in identity order have host-known positions (plan-owned table)
+  const bool identity = c.bidx == p.d_ident && p.pos_host.size() >= (size_t)p.L * p.J * 2;
 
   p.last_launches = 0;
   if (grad) {
@@ -85,17 +88,34 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const int LM = p.L * p.M;
   const dim3 row_blk(RowCfg<F>::threads), col_blk(ColCfg<F>::threads);
   const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
-  const int obj_blocks = (2 * p.sms + p.L - 1) / p.L;
 
   for (int off = 0; off < c.nbatch; off += p.B) {
     a.batch_off = off;
     a.nb = (c.nbatch - off < p.B) ? (c.nbatch - off) : p.B;
+    // region of each object the batch's patches cover (exact for the identity order, else
+    // the whole object); the object-gradient kernel tiles it
+    int max_tiles = 1;
+    for (int l = 0; l < p.L && grad; ++l) {
+      int y0 = 0, x0 = 0, y1 = p.obj_h[l], x1 = p.obj_w[l];
+      if (identity) {
+        y0 = x0 = 1 << 30;
+        y1 = x1 = -1;
+        for (int k = off; k < off + a.nb; ++k) {
+          const int y = p.pos_host[((size_t)l * p.J + k) * 2], x = p.pos_host[((size_t)l * p.J + k) * 2 + 1];
+          y0 = y < y0 ? y : y0; x0 = x < x0 ? x : x0;
+          y1 = y + F > y1 ? y + F : y1; x1 = x + F > x1 ? x + F : x1;
+        }
+      }
+      a.box[l][0] = y0; a.box[l][1] = x0; a.box[l][2] = y1; a.box[l][3] = x1;
+      const int tiles = ((y1 - y0 + kTile - 1) / kTile) * ((x1 - x0 + kTile - 1) / kTile);
+      max_tiles = tiles > max_tiles ? tiles : max_tiles;
+    }
     // forward: all chunks accumulate the model intensity
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       PTY_LAUNCH(p, kRowFwd, st,
-                 k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len, a.nb), row_blk, RowCfg<F>::smem, st>>>(
+                 k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, st>>>(
                      c.O, c.P, p.d_S, a));
       if (store)
         PTY_LAUNCH(p, kColFwd, st,
@@ -106,8 +126,9 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
                    k_col_fwd<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, st>>>(
                        p.d_S, p.d_Ipart, a, ch == 0));
     }
-    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, st>>>(a, la));
+    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<FF / kLossThreads, kLossThreads, 0, st>>>(a, la));
     if (!grad) continue;
+    if (p.remap) PTY_LAUNCH(p, kRemapAdj, st, k_remap_adj<F><<<FF / 256, 256, 0, st>>>(a, aa));
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
@@ -116,7 +137,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
                    k_col_adj<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
       } else {
         PTY_LAUNCH(p, kRowFwd, st,
-                   k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len, a.nb), row_blk, RowCfg<F>::smem, st>>>(
+                   k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, st>>>(
                        c.O, c.P, p.d_S, a));
         PTY_LAUNCH(p, kColAdj, st,
                    k_col_adj<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
@@ -124,7 +145,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       PTY_LAUNCH(p, kRowAdj, st,
                  k_row_adj<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len), row_blk, RowCfg<F>::smem, st>>>(
                      c.O, c.P, p.d_S, c.gP, a));
-      PTY_LAUNCH(p, kObjGrad, st, k_obj_grad<F><<<dim3(obj_blocks, p.L), 256, 0, st>>>(p.d_S, c.gO, a));
+      PTY_LAUNCH(p, kObjGrad, st, k_obj_grad<F><<<dim3(max_tiles, p.L), 256, 0, st>>>(p.d_S, c.gO, a));
     }
   }
   if (need_loss) {

@@ -36,6 +36,7 @@ struct ptycho_plan {
   float2* d_S = nullptr;
   float* d_Ipart = nullptr;
   float* d_D = nullptr;
+  float* d_Gt = nullptr;                       // R^T D per batch position (remap only)
   double* d_loss_part = nullptr;
   float2* d_gO = nullptr;
   float2* d_gP = nullptr;
@@ -72,7 +73,7 @@ struct CallArgs {
 };
 
 // Kernel kinds reported by ptycho_plan_profile_read (order matches PTYCHO_K_* in ptycho.h).
-enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kNumKinds };
+enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kRemapAdj, kNumKinds };
 
 // Records the start event of a profiled launch (no-op unless profiling); returns the pair index.
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);

@@ -92,7 +92,7 @@ int upload(T* dst, const T* src, long long count) {
 void free_plan(ptycho_plan* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
-                  p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_loss_part, p->d_gO, p->d_gP, p->d_status};
+                  p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -268,7 +268,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     case 256: colblocks = F / ptycho::ColCfg<256>::W; break;
     default: colblocks = F / ptycho::ColCfg<512>::W; break;
   }
-  const long long target = 2ll * p->sms;
+  const long long target = 4ll * p->sms;
   long long G = (target + (long long)colblocks * p->B - 1) / ((long long)colblocks * p->B);
   G = std::max<long long>(1, std::min<long long>(G, p->C));
   p->MG = (int)((p->C + G - 1) / G);
@@ -313,6 +313,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     std::vector<float2> w;
     std::vector<float> rt_w;
     build_remap(F, g->z, g->det_pixel, g->tilt_rad, base, w, rt_ptr, rt_idx, rt_w);
+    rc = rc ? rc : dalloc(p, &p->d_Gt, (long long)p->B * FF);
     rc = rc ? rc : dalloc(p, &p->d_tap_base, FF);
     rc = rc ? rc : dalloc(p, &p->d_tap_w, FF);
     rc = rc ? rc : dalloc(p, &p->d_rt_ptr, FF + 1);
@@ -365,7 +366,8 @@ int ptycho_plan_profile_read(ptycho_plan_t* p, double* ms, int64_t* launches) {
 }
 
 const char* ptycho_kernel_name(int kind) {
-  static const char* names[] = {"row_fwd", "col_fwd", "loss", "col_adj", "row_adj", "obj_grad", "loss_reduce", "adam"};
+  static const char* names[] = {"row_fwd", "col_fwd", "loss", "col_adj", "row_adj", "obj_grad", "loss_reduce", "adam",
+                                "remap_adj"};
   return (kind >= 0 && kind < ptycho::kNumKinds) ? names[kind] : "unknown";
 }
 
