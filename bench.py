@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scratch-mb", type=int, default=0, help="L2 scratch budget of the plan (0 = library default)")
     return ap.parse_args()
 
 
@@ -242,7 +243,7 @@ def run_ours(args, rank: int, world: int):
     plan_true.close()
     Ih = syn.poisson_measure(I_clean, 1234 + rank)
     eps = syn.default_eps(Ih)
-    plan = plan_for(w, eps=eps)
+    plan = plan_for(w, eps=eps, scratch_bytes=args.scratch_mb << 20)
     O = pack_objects(w.O0, dev)
     P = torch.as_tensor(w.P0, dtype=torch.complex64, device=dev).contiguous()
     Im = torch.as_tensor(Ih, device=dev).contiguous()

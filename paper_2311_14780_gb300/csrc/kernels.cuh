@@ -168,8 +168,7 @@ k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_
 
 // ---------------------------------------------------------------------------------------
 // measurement (f5) and loss: camera-grid prediction, masked loss partials, D = mask dL/dI.
-// One thread per camera pixel, looping over the batch (the remap taps are read once).
-// grid (F*F/256)
+// grid (F*F/256, nb)
 // ---------------------------------------------------------------------------------------
 struct LossArgs {
   const float* Ipart;            // [B][G][F][F] model grid (centred)
@@ -217,72 +216,66 @@ __global__ void __launch_bounds__(kLossThreads)
 k_loss(KArgs a, LossArgs la) {
   constexpr int FF = F * F;
   __shared__ double red[kLossThreads / 32];
+  const int b = blockIdx.y;
+  const int i = a.batch_off + b;
   const int q = blockIdx.x * kLossThreads + threadIdx.x;
-  int u = q;
-  float2 w = make_float2(0.f, 0.f);
+  const int j = batch_pos(a, i);                     // uniform over the block
+  if (j < 0) {
+    if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = 0.0;
+    if (la.D) la.D[(long long)b * FF + q] = 0.f;
+    return;
+  }
+  const float* Ip = la.Ipart + (long long)b * a.G * FF;
+  float Ic = 0.f;
   bool valid = true;
   if (la.remap) {
-    u = la.tap_base[q];
+    const int u = la.tap_base[q];
     valid = u >= 0;
-    if (valid) w = la.tap_w[q];
-  }
-  const bool mask_shared = (la.mask && !la.mask_per_frame) ? (la.mask[q] != 0) : true;
-  for (int b = 0; b < a.nb; ++b) {
-    const int i = a.batch_off + b;
-    const int j = batch_pos(a, i);                   // uniform over the block
-    double term = 0.0;
-    if (j >= 0) {
-      const float* Ip = la.Ipart + (long long)b * a.G * FF;
-      float Ic = 0.f;
-      if (valid) {
-        if (la.remap) {
-          const float i00 = model_I(Ip, la.bg, a.G, FF, u), i01 = model_I(Ip, la.bg, a.G, FF, u + 1);
-          const float i10 = model_I(Ip, la.bg, a.G, FF, u + F), i11 = model_I(Ip, la.bg, a.G, FF, u + F + 1);
-          Ic = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
-        } else {
-          Ic = model_I(Ip, la.bg, a.G, FF, q);
-        }
-      }
-      if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
-      if (la.D || la.loss_part) {
-        bool use = valid && mask_shared;
-        if (la.mask && la.mask_per_frame) use = use && (la.mask[(long long)j * FF + q] != 0);
-        float d = 0.f;
-        if (use) {
-          const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
-          const float Ie = Ic + la.eps;
-          if (la.loss_kind == 0) {
-            const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
-            term = (double)(diff * diff);
-            d = diff / se;
-          } else {
-            term = (double)poisson_term(Ie, Ih);
-            d = (Ie - Ih) / Ie;
-          }
-        }
-        if (la.D) la.D[(long long)b * FF + q] = d;
-      }
-    } else if (la.D) {
-      la.D[(long long)b * FF + q] = 0.f;
+    if (valid) {
+      const float2 w = la.tap_w[q];
+      const float i00 = model_I(Ip, la.bg, a.G, FF, u), i01 = model_I(Ip, la.bg, a.G, FF, u + 1);
+      const float i10 = model_I(Ip, la.bg, a.G, FF, u + F), i11 = model_I(Ip, la.bg, a.G, FF, u + F + 1);
+      Ic = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
     }
-    if (la.loss_part) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int wi = 0; wi < kLossThreads / 32; ++wi) s += red[wi];
-        la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = s;
+  } else {
+    Ic = model_I(Ip, la.bg, a.G, FF, q);
+  }
+  if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
+  double term = 0.0;
+  if (la.D || la.loss_part) {
+    bool use = valid;
+    if (la.mask) use = use && (la.mask[(la.mask_per_frame ? (long long)j * FF : 0) + q] != 0);
+    float d = 0.f;
+    if (use) {
+      const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
+      const float Ie = Ic + la.eps;
+      if (la.loss_kind == 0) {
+        const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
+        term = (double)(diff * diff);
+        d = diff / se;
+      } else {
+        term = (double)poisson_term(Ie, Ih);
+        d = (Ie - Ih) / Ie;
       }
-      __syncthreads();
+    }
+    if (la.D) la.D[(long long)b * FF + q] = d;
+  }
+  if (la.loss_part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int wi = 0; wi < kLossThreads / 32; ++wi) sum += red[wi];
+      la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = sum;
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // R^T of the tilted-plane remap: G[b][u] = sum over the camera pixels q that sample model
-// pixel u of w_uq D[b][q] (CSR rows in increasing q: a fixed order).   grid (F*F/256)
+// pixel u of w_uq D[b][q] (CSR rows in increasing q: a fixed order).   grid (F*F/256, nb)
 // ---------------------------------------------------------------------------------------
 struct AdjArgs {
   const float* D;                // [B][F][F] camera grid
@@ -298,13 +291,12 @@ __global__ void __launch_bounds__(256)
 k_remap_adj(KArgs a, AdjArgs aa) {
   constexpr int FF = F * F;
   const int u = blockIdx.x * 256 + threadIdx.x;
+  const int b = blockIdx.y;
   const int e0 = __ldg(aa.rt_ptr + u), e1 = __ldg(aa.rt_ptr + u + 1);
-  for (int b = 0; b < a.nb; ++b) {
-    const float* Db = aa.D + (long long)b * FF;
-    float gv = 0.f;
-    for (int e = e0; e < e1; ++e) gv = fmaf(__ldg(aa.rt_w + e), Db[__ldg(aa.rt_idx + e)], gv);
-    aa.Gt[(long long)b * FF + u] = gv;
-  }
+  const float* Db = aa.D + (long long)b * FF;
+  float gv = 0.f;
+  for (int e = e0; e < e1; ++e) gv = fmaf(__ldg(aa.rt_w + e), Db[__ldg(aa.rt_idx + e)], gv);
+  aa.Gt[(long long)b * FF + u] = gv;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -436,15 +428,20 @@ k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
     if (y < 0 || y >= oy0 + kTile || y + F <= oy0 || x >= ox0 + kTile || x + F <= ox0) continue;
     const bool in_x = ox >= x && ox < x + F;
     const float2* src = S + ((long long)b * a.C + (mlo - a.chunk_base)) * F * F + (ox - x);
-    for (int mode = mlo; mode < mhi; ++mode, src += (long long)F * F) {
-      float2 v[kTile / 8];
+    for (int m0 = mlo; m0 < mhi; m0 += 4, src += 4ll * F * F) {
+      float2 v[4][kTile / 8];
 #pragma unroll
-      for (int k = 0; k < kTile / 8; ++k) {
-        const int oy = oy0 + ty0 + 8 * k;
-        v[k] = (in_x && oy >= y && oy < y + F) ? src[(long long)(oy - y) * F] : make_float2(0.f, 0.f);
-      }
+      for (int mm = 0; mm < 4; ++mm)
 #pragma unroll
-      for (int k = 0; k < kTile / 8; ++k) acc[k] = cadd(acc[k], v[k]);
+        for (int k = 0; k < kTile / 8; ++k) {
+          const int oy = oy0 + ty0 + 8 * k;
+          const bool ok = m0 + mm < mhi && in_x && oy >= y && oy < y + F;
+          v[mm][k] = ok ? src[(long long)mm * F * F + (long long)(oy - y) * F] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm)
+#pragma unroll
+        for (int k = 0; k < kTile / 8; ++k) acc[k] = cadd(acc[k], v[mm][k]);
     }
   }
   float2* g = gO + a.obj_off[l];

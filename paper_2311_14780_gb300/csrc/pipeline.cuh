@@ -126,9 +126,9 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
                    k_col_fwd<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, st>>>(
                        p.d_S, p.d_Ipart, a, ch == 0));
     }
-    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<FF / kLossThreads, kLossThreads, 0, st>>>(a, la));
+    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, st>>>(a, la));
     if (!grad) continue;
-    if (p.remap) PTY_LAUNCH(p, kRemapAdj, st, k_remap_adj<F><<<FF / 256, 256, 0, st>>>(a, aa));
+    if (p.remap) PTY_LAUNCH(p, kRemapAdj, st, k_remap_adj<F><<<dim3(FF / 256, a.nb), 256, 0, st>>>(a, aa));
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
