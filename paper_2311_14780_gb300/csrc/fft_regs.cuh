@@ -148,7 +148,8 @@ struct Xch {
 };
 
 // Forward 1D FFT, layout I -> layout O.  ``x`` has N2 slots; ``xc`` is this vector's
-// exchange region; ``tw`` is the table W_F^(t*k2) as tw[t*N2 + k2].  SYNC is the barrier
+// exchange region; ``tw`` is the table W_F^(t*k2) stored as tw[k2*N1 + t], so the N1 threads of
+// one vector read a contiguous run.  SYNC is the barrier
 // used between the exchange write and read (warp or block).
 template <int F, class Sync>
 __device__ __forceinline__ void fft_fwd_I2O(float2 (&x)[FftShape<F>::N2], int t, float2* xc,
@@ -156,7 +157,7 @@ __device__ __forceinline__ void fft_fwd_I2O(float2 (&x)[FftShape<F>::N2], int t,
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2;
   Dft<N2, 1, false>::run(x);
 #pragma unroll
-  for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmul(x[k2], __ldg(tw + t * N2 + k2));
+  for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmul(x[k2], __ldg(tw + k2 * N1 + t));
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) xc[Xch<F>::idx(k2, t)] = x[k2];
   sync();
@@ -185,7 +186,7 @@ __device__ __forceinline__ void fft_inv_O2I(float2 (&x)[FftShape<F>::N2], int t,
   for (int k2 = 0; k2 < N2; ++k2) x[k2] = xc[Xch<F>::idx(k2, t)];
   sync();
 #pragma unroll
-  for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmulc(x[k2], __ldg(tw + t * N2 + k2));
+  for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmulc(x[k2], __ldg(tw + k2 * N1 + t));
   Dft<N2, 1, true>::run(x);
 }
 

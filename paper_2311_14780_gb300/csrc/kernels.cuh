@@ -345,18 +345,33 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
 
 // ---------------------------------------------------------------------------------------
 // adjoint row pass: chi = dL/dpsi; probe gradient summed over the batch; object-gradient
-// contributions conj(sigma P) chi left in S.   grid (F/RPB, chunk_len)
+// contributions conj(sigma P) chi left in S.  The batch is split over kAdjSlots groups of
+// warps (slot s takes positions s, s + kAdjSlots, ...); their probe-gradient sums are added
+// in slot order through shared memory, so the result does not depend on timing.
+// grid (F/RPB, chunk_len)
 // ---------------------------------------------------------------------------------------
+constexpr int kAdjSlots = 4;
+template <int F> struct RowAdjCfg {
+  static constexpr int T = FftShape<F>::N1;
+  static constexpr int RPB = 256 / (T * kAdjSlots);   // rows per block
+  static constexpr int threads = RPB * T * kAdjSlots;
+  static constexpr int vecs = RPB * kAdjSlots;
+  static constexpr int smem_xch = vecs * Xch<F>::region_rows * (int)sizeof(float2);
+  static constexpr int smem_red = (kAdjSlots - 1) * RPB * F * (int)sizeof(float2);
+  static constexpr int smem = smem_xch > smem_red ? smem_xch : smem_red;
+};
+
 template <int F>
-__global__ void __launch_bounds__(RowCfg<F>::threads)
+__global__ void __launch_bounds__(RowAdjCfg<F>::threads)
 k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
           float2* __restrict__ gP, KArgs a) {
-  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowCfg<F>::T;
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowAdjCfg<F>::T, RPB = RowAdjCfg<F>::RPB;
   extern __shared__ float2 smem[];
   __shared__ int2 spos[kMaxB];
   __shared__ float ssig[kMaxB];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
-  const int r = blockIdx.x * RowCfg<F>::RPB + vec;
+  const int slot = vec / RPB, rr = vec % RPB;
+  const int r = blockIdx.x * RPB + rr;
   const int cm = blockIdx.y;
   const int mode = a.chunk_base + cm;
   const int l = mode / a.M;
@@ -370,9 +385,9 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
     pr[n2] = __ldg(Prow + t + N1 * n2);
     acc[n2] = make_float2(0.f, 0.f);
   }
-  for (int b = 0; b < a.nb; ++b) {
+  for (int b = slot; b < a.nb; b += kAdjSlots) {
     const int2 yx = spos[b];
-    if (yx.x < 0) continue;                           // uniform over the block
+    if (yx.x < 0) continue;                           // uniform over the slot's warps
     const float s = ssig[b];
     float2* row = S + (((long long)b * a.C + cm) * F + r) * F;
     const float2* Orow = Ol + (long long)(yx.x + r) * Wl + yx.y;
@@ -390,11 +405,23 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
       row[t + N1 * n2] = cscale(cconjmul(pr[n2], v[n2]), s);     // conj(sigma P) chi
     }
   }
-  float2* g = gP + ((long long)mode * F + r) * F;
+  // slots 1.. hand their sums to slot 0 through shared memory (the exchange area is free now)
+  __syncthreads();
+  float2* red = smem;                                 // [kAdjSlots-1][RPB][F]
+  if (slot > 0) {
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) {
-    const int c = t + N1 * n2;
-    g[c] = cadd(g[c], acc[n2]);
+    for (int n2 = 0; n2 < N2; ++n2) red[((slot - 1) * RPB + rr) * F + t + N1 * n2] = acc[n2];
+  }
+  __syncthreads();
+  if (slot == 0) {
+    float2* g = gP + ((long long)mode * F + r) * F;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      const int c = t + N1 * n2;
+      float2 sum = acc[n2];
+      for (int s2 = 1; s2 < kAdjSlots; ++s2) sum = cadd(sum, red[((s2 - 1) * RPB + rr) * F + c]);
+      g[c] = cadd(g[c], sum);
+    }
   }
 }
 

@@ -107,7 +107,7 @@ extern "C" int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J
   for (int t = 0; t < N1; ++t)
     for (int k2 = 0; k2 < N2; ++k2) {
       const double ang = -2.0 * 3.14159265358979323846 * (double)((t * k2) % F) / (double)F;
-      tw[t * N2 + k2] = make_float2((float)cos(ang), (float)sin(ang));
+      tw[k2 * N1 + t] = make_float2((float)cos(ang), (float)sin(ang));
     }
   if (cudaMemcpyAsync(base + off_tw, tw, sizeof(float2) * (size_t)F, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(base + off_pos, pos, sizeof(int32_t) * (size_t)L * J * 2, cudaMemcpyHostToDevice, st) !=

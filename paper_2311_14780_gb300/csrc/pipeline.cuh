@@ -23,7 +23,7 @@ int prepare_kernels() {
   const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(k_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowAdjCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
@@ -143,8 +143,8 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
                    k_col_adj<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
       }
       PTY_LAUNCH(p, kRowAdj, st,
-                 k_row_adj<F><<<dim3(F / RowCfg<F>::RPB, a.chunk_len), row_blk, RowCfg<F>::smem, st>>>(
-                     c.O, c.P, p.d_S, c.gP, a));
+                 k_row_adj<F><<<dim3(F / RowAdjCfg<F>::RPB, a.chunk_len), RowAdjCfg<F>::threads, RowAdjCfg<F>::smem,
+                                st>>>(c.O, c.P, p.d_S, c.gP, a));
       PTY_LAUNCH(p, kObjGrad, st, k_obj_grad<F><<<dim3(max_tiles, p.L), 256, 0, st>>>(p.d_S, c.gO, a));
     }
   }

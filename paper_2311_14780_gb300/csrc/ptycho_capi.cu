@@ -291,7 +291,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
 
   std::vector<int32_t> ident(g->J);
   for (int j = 0; j < g->J; ++j) ident[j] = j;
-  // twiddles W_F^(t*k2) of the two-stage FFT, tw[t*N2 + k2], in FP64 then rounded
+  // twiddles W_F^(t*k2) of the two-stage FFT, tw[k2*N1 + t], in FP64 then rounded
   int N1 = 0, N2 = 0;
   switch (F) {
     case 64: N1 = ptycho::FftShape<64>::N1; N2 = ptycho::FftShape<64>::N2; break;
@@ -303,7 +303,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   for (int t = 0; t < N1; ++t)
     for (int k2 = 0; k2 < N2; ++k2) {
       const double ang = -2.0 * kPi * (double)((t * k2) % F) / (double)F;
-      tw[(size_t)t * N2 + k2] = make_float2((float)cos(ang), (float)sin(ang));
+      tw[(size_t)k2 * N1 + t] = make_float2((float)cos(ang), (float)sin(ang));
     }
   rc = rc ? rc : upload(p->d_pos, p->pos_host.data(), (long long)p->pos_host.size());
   rc = rc ? rc : upload(p->d_ident, ident.data(), g->J);
