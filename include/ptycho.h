@@ -48,6 +48,7 @@ extern "C" {
 #define PTYCHO_ETIMEDOUT (-5)    /* a bounded device wait ran out (serving loop)       */
 #define PTYCHO_EUNSUPPORTED (-6) /* frame size not in {64, 128, 256, 512}, L > 16      */
 #define PTYCHO_ETOOLARGE (-7)    /* problem does not fit ptycho_forward_noalloc's array */
+#define PTYCHO_EBUSY (-8)        /* serving: no free slot, or the HBM budget is exhausted  */
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */
@@ -145,6 +146,61 @@ int64_t ptycho_plan_last_launches(const ptycho_plan_t* plan);
  * skipped.  Synchronises the device (call it outside the timed loop). */
 #define PTYCHO_STATUS_BAD_INDEX 1
 int ptycho_plan_status(ptycho_plan_t* plan, int32_t* flags);
+
+/* Plain (unfused) form of ptycho_step, the baseline the fused path is measured against:
+ * every stage (gather, row DFT, column DFT, intensity, loss, R^T, multiply, inverse DFTs,
+ * gradient scatter) is a separate kernel, exit waves go through a device buffer that the
+ * call allocates (stream-ordered), and gradients are scattered with FP32 atomics (so their
+ * summation order, and the last bits of the result, can vary between runs).  Arguments as
+ * for ptycho_step with all positions. */
+int ptycho_plain_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, const float* sigma,
+                      const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
+                      double* loss_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Multi-site serving (continuous batching).  The paper reconstructs one dataset at a time;
+ * this serves many reconstructions ("sites") of different F, J, L, M at once on one GPU.
+ * Each admitted site keeps its plan, Adam moments (zero at admission), a device step
+ * counter and its loss resident, and owns a CUDA graph of one iteration (ptycho_step over
+ * all its positions) captured at admission.  ptycho_server_tick runs one iteration of every
+ * active site as a single graph launch whose per-site branches have no dependencies, so the
+ * sites' kernels overlap on the device.  Sites are admitted between ticks while the HBM
+ * budget allows (their plan, moments and the caller's resident O, P, I_meas and mask count
+ * against it) and give their memory back with ptycho_server_release.  Results of a site
+ * do not depend on the other sites in the mix (no shared buffers, fixed-order reductions).
+ * Host-driven: no kernel waits on another. */
+typedef struct ptycho_server ptycho_server_t;
+
+typedef struct {
+  float* O; float* P;            /* DEVICE parameters, updated in place every iteration     */
+  const float* I_meas;           /* DEVICE [J][F][F]                                        */
+  const uint8_t* mask;           /* DEVICE mask or NULL, as for ptycho_loss                 */
+  int32_t mask_per_frame;
+  const float* sigma;            /* DEVICE [J] or NULL                                      */
+  const float* bg;               /* DEVICE [F][F] or NULL                                   */
+  float lr_O, lr_P, beta1, beta2, eps;   /* Adam hyper-parameters                           */
+  int32_t iterations;            /* iterations to run before the site is done               */
+} ptycho_site_t;
+
+/* A server for the current device with a budget of device bytes and at most max_sites. */
+int ptycho_server_create(int64_t hbm_budget_bytes, int32_t max_sites, ptycho_server_t** out);
+/* Synchronises the device, frees every site and the server.  NULL is accepted. */
+int ptycho_server_destroy(ptycho_server_t* server);
+/* Validates and plans a site, checks the budget (PTYCHO_EBUSY when it does not fit or no
+ * slot is free; nothing stays allocated then), allocates its state and captures its
+ * iteration graph.  *slot receives the site's slot.  Synchronous. */
+int ptycho_server_admit(ptycho_server_t* server, const ptycho_geom_t* geom, const ptycho_site_t* site,
+                        int32_t* slot);
+/* Enqueues one iteration of every site that has iterations left, as one graph launch on
+ * stream; *n_sites (may be NULL) receives how many sites it covered. */
+int ptycho_server_tick(ptycho_server_t* server, void* stream, int32_t* n_sites);
+/* Iterations enqueued so far and the loss of the last completed iteration (HOST double;
+ * the copy synchronises with the device).  Either pointer may be NULL. */
+int ptycho_server_site_status(ptycho_server_t* server, int32_t slot, int32_t* iters_done, double* loss);
+/* Waits for the device, then frees the site's plan and state and returns its budget. */
+int ptycho_server_release(ptycho_server_t* server, int32_t slot);
+/* Bytes currently counted against the budget. */
+int64_t ptycho_server_used_bytes(const ptycho_server_t* server);
 
 /* Opt-in per-kernel timing.  While enabled, every launch of a compute call is bracketed
  * by a CUDA event pair recorded on the call's stream.  ptycho_plan_profile_read waits for

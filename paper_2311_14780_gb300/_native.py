@@ -33,6 +33,15 @@ class Adam(ctypes.Structure):
     ]
 
 
+class Site(ctypes.Structure):
+    _fields_ = [
+        ("O", ctypes.c_void_p), ("P", ctypes.c_void_p), ("I_meas", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+        ("mask_per_frame", ctypes.c_int32), ("sigma", ctypes.c_void_p), ("bg", ctypes.c_void_p),
+        ("lr_O", ctypes.c_float), ("lr_P", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+        ("eps", ctypes.c_float), ("iterations", ctypes.c_int32),
+    ]
+
+
 # (name, restype, argtypes) of every exported entry point
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
@@ -53,6 +62,14 @@ SIGNATURES = [
     ("ptycho_kernel_name", ctypes.c_char_p, [_I]),
     ("ptycho_forward_noalloc", _I, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_int32_p,
                                     c_int32_p, c_int32_p, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ptycho_plain_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _VP]),
+    ("ptycho_server_create", _I, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_VP)]),
+    ("ptycho_server_destroy", _I, [_VP]),
+    ("ptycho_server_admit", _I, [_VP, ctypes.POINTER(Geom), ctypes.POINTER(Site), c_int32_p]),
+    ("ptycho_server_tick", _I, [_VP, _VP, c_int32_p]),
+    ("ptycho_server_site_status", _I, [_VP, ctypes.c_int32, c_int32_p, c_double_p]),
+    ("ptycho_server_release", _I, [_VP, ctypes.c_int32]),
+    ("ptycho_server_used_bytes", ctypes.c_int64, [_VP]),
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 

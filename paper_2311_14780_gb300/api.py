@@ -53,6 +53,30 @@ def unpack_objects(flat: torch.Tensor, shapes) -> list:
     return out
 
 
+def geom_struct(F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = "amplitude", eps: float = 0.0,
+                remap: bool = False, z: float = 88e-3, det_pixel: float = 15e-6,
+                tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0):
+    """A ``ptycho_geom_t`` and the host arrays it points to (keep both alive while used)."""
+    keep = {
+        "h": np.ascontiguousarray([int(s_[0]) for s_ in obj_shapes], dtype=np.int32),
+        "w": np.ascontiguousarray([int(s_[1]) for s_ in obj_shapes], dtype=np.int32),
+        "pos": np.ascontiguousarray(np.asarray(pos, dtype=np.int32).reshape(L, J, 2)),
+        "lam": None if lambdas is None else np.ascontiguousarray(lambdas, dtype=np.float64),
+    }
+    g = _native.Geom()
+    g.L, g.M, g.F, g.J = int(L), int(M), int(F), int(J)
+    g.obj_h = keep["h"].ctypes.data_as(_native.c_int32_p)
+    g.obj_w = keep["w"].ctypes.data_as(_native.c_int32_p)
+    g.pos = keep["pos"].ctypes.data_as(_native.c_int32_p)
+    g.lam = None if keep["lam"] is None else keep["lam"].ctypes.data_as(_native.c_double_p)
+    g.z, g.det_pixel, g.tilt_rad = float(z), float(det_pixel), float(tilt_rad)
+    g.remap = 1 if remap else 0
+    g.loss = LOSS_CODES[loss]
+    g.eps = float(eps)
+    g.scratch_bytes = int(scratch_bytes)
+    return g, keep
+
+
 class Plan:
     """A validated problem geometry with its device workspace (``ptycho_plan_t``)."""
 
@@ -62,21 +86,9 @@ class Plan:
         self.F, self.L, self.M, self.J = int(F), int(L), int(M), int(J)
         self.obj_shapes = [(int(h), int(w)) for (h, w) in obj_shapes]
         self.loss_kind = loss
-        self._h = np.ascontiguousarray([s[0] for s in self.obj_shapes], dtype=np.int32)
-        self._w = np.ascontiguousarray([s[1] for s in self.obj_shapes], dtype=np.int32)
-        self._pos = np.ascontiguousarray(np.asarray(pos, dtype=np.int32).reshape(L, J, 2))
-        self._lam = None if lambdas is None else np.ascontiguousarray(lambdas, dtype=np.float64)
-        g = _native.Geom()
-        g.L, g.M, g.F, g.J = self.L, self.M, self.F, self.J
-        g.obj_h = self._h.ctypes.data_as(_native.c_int32_p)
-        g.obj_w = self._w.ctypes.data_as(_native.c_int32_p)
-        g.pos = self._pos.ctypes.data_as(_native.c_int32_p)
-        g.lam = None if self._lam is None else self._lam.ctypes.data_as(_native.c_double_p)
-        g.z, g.det_pixel, g.tilt_rad = float(z), float(det_pixel), float(tilt_rad)
-        g.remap = 1 if remap else 0
-        g.loss = LOSS_CODES[loss]
-        g.eps = float(eps)
-        g.scratch_bytes = int(scratch_bytes)
+        g, self._keep = geom_struct(F, L, M, J, obj_shapes, pos, loss=loss, eps=eps, remap=remap, z=z,
+                                    det_pixel=det_pixel, tilt_rad=tilt_rad, lambdas=lambdas,
+                                    scratch_bytes=scratch_bytes)
         self._geom = g
         h = ctypes.c_void_p()
         _check(_native.lib().ptycho_plan_create(ctypes.byref(g), ctypes.byref(h)), "ptycho_plan_create")
@@ -232,6 +244,24 @@ class Plan:
         return loss_out
 
 
+    def plain_step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, loss_out=None,
+                   stream=None):
+        """ptycho_plain_step: the unfused baseline of ``step`` over all positions."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        m, mpf = self._mask(mask)
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float64, device=self.device)
+        st = state.c_struct()
+        rc = _native.lib().ptycho_plain_step(self._h_plan, ctypes.byref(st), _ptr(Or), _ptr(Pr),
+                                             _ptr(self._f32(sigma, self.J, "sigma")), _ptr(self._f32(bg, FF, "bg")),
+                                             _ptr(self._f32(Imeas, self.J * FF, "Imeas")), _ptr(m), mpf,
+                                             _ptr(loss_out), _stream_handle(stream))
+        _check(rc, "ptycho_plain_step")
+        state.t = int(st.t)
+        return loss_out
+
+
 class AdamState:
     """Adam moments for O and P (device tensors, 2 floats per complex element)."""
 
@@ -251,6 +281,12 @@ class AdamState:
         s.mO, s.vO = self.mO.data_ptr(), self.vO.data_ptr()
         s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
         return s
+
+
+def plan_geometry_plan(r, **kw) -> Plan:
+    """Plan for a serving request (``serve.Request``)."""
+    return Plan(r.F, r.L, r.M, r.J, r.obj_shapes, r.pos, loss=r.loss, eps=r.eps, remap=r.remap, z=r.z,
+                det_pixel=r.det_pixel, tilt_rad=r.tilt_rad, **kw)
 
 
 def plan_for(w, **kw) -> Plan:

@@ -1,7 +1,10 @@
-// Kernels and pipeline instantiated for 512x512 frames.
+// Kernels and pipelines instantiated for 512x512 frames.
 #include "pipeline.cuh"
+#include "plain.cuh"
 
 namespace ptycho {
 template int run_pipeline<512>(ptycho_plan& p, const CallArgs& c, cudaStream_t st);
 template int prepare_kernels<512>();
+template int plain_adjoint<512>(ptycho_plan& p, const CallArgs& c, float2* psi, float* Ibuf, float* Dbuf, float* Gbuf,
+                                int Bp, cudaStream_t st);
 }  // namespace ptycho

@@ -82,5 +82,8 @@ void prof_end(ptycho_plan& p, long long idx, cudaStream_t st);
 // Defined once per frame size in kern_<F>.cu.
 template <int F> int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st);
 template <int F> int prepare_kernels();
+// Plain (unfused) adjoint of one site, in plain.cuh; psi, Ibuf, Dbuf and Gbuf hold Bp positions.
+template <int F> int plain_adjoint(ptycho_plan& p, const CallArgs& c, float2* psi, float* Ibuf, float* Dbuf,
+                                   float* Gbuf, int Bp, cudaStream_t st);
 
 }  // namespace ptycho

@@ -200,6 +200,7 @@ const char* ptycho_strerror(int code) {
     case PTYCHO_ETIMEDOUT: return "a bounded device wait timed out";
     case PTYCHO_EUNSUPPORTED: return "unsupported configuration (frame size or wavelength count)";
     case PTYCHO_ETOOLARGE: return "problem does not fit the fixed array of the allocation-free entry point";
+    case PTYCHO_EBUSY: return "no free serving slot, or the HBM budget is exhausted";
   }
   return "unknown error";
 }
