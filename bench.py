@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scratch-mb", type=int, default=0, help="L2 scratch budget of the plan (0 = library default)")
+    ap.add_argument("--requests", type=int, default=64, help="config5: number of serving requests")
+    ap.add_argument("--iterations", type=int, default=20, help="config5: iterations per request")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="config5: HBM budget of the server")
+    ap.add_argument("--no-plain", action="store_true", help="config5: skip the plain one-site-at-a-time run")
+    ap.add_argument("--plain", action="store_true", help="time the plain unfused step instead of the fused one")
+    ap.add_argument("--tick-evals", type=int, default=32768,
+                    help="config5: admit while the active sites' evaluations per tick stay within this (0 = no cap)")
     return ap.parse_args()
 
 
@@ -254,7 +261,10 @@ def run_ours(args, rank: int, world: int):
     evals = w.n_evals
 
     def step():
-        plan.step(st, O, P, Im, loss_out=loss)
+        if args.plain:
+            plan.plain_step(st, O, P, Im, loss_out=loss)
+        else:
+            plan.step(st, O, P, Im, loss_out=loss)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -371,12 +381,73 @@ def run_ours(args, rank: int, world: int):
     return 0
 
 
+def serving_requests(args, dev):
+    """Config 5: Poisson arrivals (mean 50 ms); F in {128, 256, 512}, J in [100, 900], L in 1..5,
+    M in 1..8; flat-object / elliptical-aperture start.  Measured data: our forward model on
+    the truth plus Poisson noise drawn on the GPU (input synthesis, outside every timing)."""
+    import torch
+    from paper_2311_14780_gb300 import pack_objects, plan_for
+    from paper_2311_14780_gb300.serve import Request
+    from synthetic import workloads as syn
+    bank = syn.TextureBank()
+    gen = torch.Generator(device=dev).manual_seed(5)
+    served, plain = [], []
+    for d in syn.config5_requests(n=args.requests):
+        w = syn.serving_request_inputs(d, bank)
+        pt = plan_for(w, eps=0.0)
+        I = pt.forward(pack_objects(w.O_true, dev), torch.as_tensor(w.P_true, dtype=torch.complex64, device=dev))
+        pt.close()
+        Ih = torch.poisson(I.clamp_min(0), generator=gen).contiguous()
+        eps = 1e-9 * float(Ih.mean().item())
+        O0 = pack_objects(w.O0, dev)
+        P0 = torch.as_tensor(w.P0, dtype=torch.complex64, device=dev).contiguous()
+        for out in (served, plain):
+            out.append(Request(w.name, d["arrival_s"], w.F, w.L, w.M, w.J, w.obj_shapes, w.pos, O0.clone(),
+                               P0.clone(), Ih, iterations=args.iterations, loss="poisson", eps=eps, remap=True,
+                               lr_O=1e-2, lr_P=1e-2))
+    torch.cuda.synchronize()
+    return served, plain
+
+
+def run_serving(args, rank: int, world: int):
+    import torch
+    from paper_2311_14780_gb300.serve import plain_stream, serve_stream
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    served, plain = serving_requests(args, dev)
+    clocks = ClockSampler(local)
+    time.sleep(0.2)
+    clocks.mark_start()
+    s_sum = serve_stream(served, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None)
+    clocks.mark_end()
+    clk = clocks.stop()
+    p_sum = None
+    if not args.no_plain:
+        p_sum = plain_stream(plain)
+        rel = [abs(a.final_loss - b.final_loss) / max(abs(b.final_loss), 1e-300) for a, b in zip(served, plain)]
+        p_sum["final_loss_rel_diff_max"] = max(rel)
+    if rank == 0:
+        line = {"metric": METRIC, "value": s_sum["evals_per_s"], "unit": UNIT, "n_gpus": world,
+                "steps": args.iterations, "warmup": 0, "ms_per_step": s_sum["iter_ms_p50"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (loss sum f64)", "data": "synthetic",
+                "config": {"workload": f"config5: serving stream of {args.requests} requests, Poisson arrivals "
+                                       f"(mean 50 ms), F in {{128,256,512}}, J in [100,900], L 1-5, M 1-8, "
+                                       f"{args.iterations} iterations each, HBM budget {args.budget_gb} GB"},
+                "clocks": clk, "serving": s_sum, "plain": p_sum,
+                "served_over_plain": (s_sum["evals_per_s"] / p_sum["evals_per_s"]) if p_sum else None}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.config == "config5":
+        return run_serving(args, rank, world)
     return run_ours(args, rank, world)
 
 

@@ -73,7 +73,8 @@ typedef struct {
   int32_t remap;            /* 1: apply the tilted-plane remap inside f5; 0: identity   */
   int32_t loss;             /* PTYCHO_LOSS_AMPLITUDE or PTYCHO_LOSS_POISSON             */
   float eps;                /* intensity floor added to I in the loss and its gradient  */
-  int64_t scratch_bytes;    /* L2-resident FFT scratch budget; 0 = library default      */
+  int64_t scratch_bytes;    /* FFT scratch budget in bytes; 0 = library default (about 128
+                               evaluations per batch, at most 2 GiB)                  */
 } ptycho_geom_t;
 
 /* Adam state (Kingma & Ba), cited by the paper as its optimiser.  Real and imaginary

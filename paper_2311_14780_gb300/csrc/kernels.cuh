@@ -28,7 +28,7 @@ namespace ptycho {
 constexpr int kMaxL = 16;
 constexpr int kLossThreads = 256;
 constexpr int kTile = 32;        // object-gradient tile side
-constexpr int kMaxB = 32;        // positions per batch (upper bound)
+constexpr int kMaxB = 128;       // positions per batch (upper bound; <= threads of the staging blocks)
 
 struct KArgs {
   int L, M, F, J;

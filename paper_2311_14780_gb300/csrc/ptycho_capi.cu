@@ -64,7 +64,8 @@ using ptycho::CallKind;
 
 namespace {
 
-constexpr long long kDefaultScratch = 64ll << 20;   // L2-resident FFT scratch (L2 = 126 MiB)
+constexpr long long kMaxScratch = 2ll << 30;   // default upper bound of the FFT scratch
+constexpr long long kBatchEvals = 128;         // evaluations per batch the default aims for
 constexpr double kPi = 3.14159265358979323846;
 
 bool supported_F(int F) { return F == 64 || F == 128 || F == 256 || F == 512; }
@@ -245,16 +246,22 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   p->P_numel = (long long)g->L * g->M * F * F;
   p->pos_host.assign(g->pos, g->pos + (size_t)g->L * g->J * 2);
 
-  // batching: keep every mode's field of B positions in scratch when it fits the budget,
-  // otherwise one position at a time with the modes split into chunks (recomputed later).
+  // batching: a batch keeps the fields of all L*M modes of B positions in the scratch (store
+  // mode, no recompute) with B chosen so that one launch carries about kBatchEvals
+  // evaluations; a small scratch stays in L2, a large one spills to HBM, which costs less than
+  // launching small batches.  Only when one position's fields exceed the budget are the modes
+  // split into chunks that the adjoint recomputes.  An explicit scratch_bytes fits as many
+  // positions as the budget holds.
   const long long FF8 = (long long)F * F * (long long)sizeof(float2);
   const long long LM = (long long)g->L * g->M;
-  p->scratch_budget = g->scratch_bytes > 0 ? g->scratch_bytes : kDefaultScratch;
+  p->scratch_budget = g->scratch_bytes > 0 ? g->scratch_bytes : kMaxScratch;
   if (LM * FF8 <= p->scratch_budget) {
     p->store = 1;
     p->C = (int)LM;
     p->nchunks = 1;
-    p->B = (int)std::max<long long>(1, std::min<long long>(32, p->scratch_budget / (LM * FF8)));
+    long long B = p->scratch_budget / (LM * FF8);
+    if (g->scratch_bytes <= 0) B = std::min<long long>(B, (kBatchEvals + LM - 1) / LM);
+    p->B = (int)std::max<long long>(1, std::min<long long>(B, ptycho::kMaxB));
     p->B = std::min(p->B, g->J);
   } else {
     p->store = 0;

@@ -131,6 +131,8 @@ struct ptycho_server {
   cudaStream_t cap = nullptr;                 // capture stream
   cudaGraphExec_t exec = nullptr;             // parent graph of the last active set
   std::vector<int> exec_set;
+  long long epoch = 0;                        // bumped by every admission and release: a slot
+  long long exec_epoch = -1;                  // number can be reused by a different site
   long long last_launch_nodes = 0;
 };
 
@@ -220,6 +222,7 @@ int ptycho_server_admit(ptycho_server_t* sv, const ptycho_geom_t* geom, const pt
   s->graph = g;
   sv->slots[(size_t)slot] = s;
   sv->used += s->bytes;
+  sv->epoch += 1;
   *slot_out = slot;
   return PTYCHO_OK;
 }
@@ -233,7 +236,7 @@ int ptycho_server_tick(ptycho_server_t* sv, void* stream, int32_t* n_sites) {
   }
   if (n_sites) *n_sites = (int32_t)active.size();
   if (active.empty()) return PTYCHO_OK;
-  if (!sv->exec || active != sv->exec_set) {
+  if (!sv->exec || sv->exec_epoch != sv->epoch || active != sv->exec_set) {
     if (sv->exec) {
       cudaGraphExecDestroy(sv->exec);
       sv->exec = nullptr;
@@ -255,6 +258,7 @@ int ptycho_server_tick(ptycho_server_t* sv, void* stream, int32_t* n_sites) {
       return PTYCHO_ECUDA;
     }
     sv->exec_set = active;
+    sv->exec_epoch = sv->epoch;
   }
   if (cudaGraphLaunch(sv->exec, (cudaStream_t)stream) != cudaSuccess) return PTYCHO_ECUDA;
   for (int i : active) sv->slots[(size_t)i]->iters_done += 1;
@@ -277,6 +281,11 @@ int ptycho_server_release(ptycho_server_t* sv, int32_t slot) {
   Site* s = sv->slots[(size_t)slot];
   sv->used -= s->bytes;
   sv->slots[(size_t)slot] = nullptr;
+  sv->epoch += 1;
+  if (sv->exec) {                             // it may contain this site's graph
+    cudaGraphExecDestroy(sv->exec);
+    sv->exec = nullptr;
+  }
   free_site(s);
   return PTYCHO_OK;
 }

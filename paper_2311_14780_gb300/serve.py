@@ -57,6 +57,10 @@ class Request:
     def evals(self) -> int:
         return self.J * self.L * self.M * self.iterations
 
+    @property
+    def evals_per_iteration(self) -> int:
+        return self.J * self.L * self.M
+
 
 class Server:
     """``ptycho_server_t``: resident sites, budgeted admission, one graph launch per tick."""
@@ -123,11 +127,15 @@ class Server:
             pass
 
 
-def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, realtime: bool = True) -> dict:
+def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, realtime: bool = True,
+                 max_tick_evals: Optional[int] = None) -> dict:
     """Run the requests through a Server, admitting them as they arrive and fit.
 
-    With ``realtime`` the arrival times are honoured against the wall clock; otherwise all
-    requests are present at time 0.  Returns the latency and throughput summary.
+    Requests are admitted in arrival order while the HBM budget allows and, if
+    ``max_tick_evals`` is set, while the active sites' evaluations per tick stay within it
+    (a request is always admitted when nothing is active).  With ``realtime`` the arrival
+    times are honoured against the wall clock; otherwise all requests are present at time
+    0.  Returns the latency and throughput summary.
     """
     sv = Server(budget_bytes, max_sites)
     stream = torch.cuda.current_stream()
@@ -140,6 +148,9 @@ def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, r
         now = time.perf_counter() - t0
         while pending and (not realtime or pending[0].arrival_s <= now):
             r = pending[0]
+            load = sum(a.evals_per_iteration for a in active.values())
+            if active and max_tick_evals is not None and load + r.evals_per_iteration > max_tick_evals:
+                break
             slot = sv.admit(r)
             if slot is None:
                 if not active:
@@ -168,7 +179,7 @@ def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, r
     makespan = max(r.done_s for r in reqs) - min(r.arrival_s for r in reqs) if realtime else \
         max(r.done_s for r in reqs)
     sv.close()
-    return summarize(reqs, makespan, ticks=ticks)
+    return summarize(reqs, makespan, ticks=ticks, max_tick_evals=max_tick_evals)
 
 
 def plain_stream(reqs: List[Request], realtime: bool = True) -> dict:

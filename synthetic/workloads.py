@@ -29,7 +29,7 @@ __all__ = [
     "gaussian_amplitude", "probe_modes", "elliptical_aperture_modes",
     "object_smooth", "object_rectangles", "raster_positions", "scale_positions",
     "round_half_away", "poisson_measure", "default_eps", "config1", "config2", "near_truth",
-    "serving_workload",
+    "serving_workload", "serving_request_inputs", "TextureBank",
     "config3", "config4", "config5_requests", "tiny_workload", "CONFIG3_GRID",
 ]
 
@@ -383,6 +383,45 @@ def config5_requests(n: int = 64, seed: int = 5, mean_interval_s: float = 0.05,
                         L=int(r.integers(1, l_max + 1)), M=int(r.integers(1, m_max + 1)),
                         seed=1000 + i))
     return out
+
+
+class TextureBank:
+    """One large complex texture (rectangles on a smooth background) that serving requests
+    crop their objects from, so that a stream of many requests is generated quickly."""
+
+    def __init__(self, side: int = 2304, seed: int = 99):
+        rng = np.random.default_rng(seed)
+        self.tex = object_rectangles(rng, side, side, [PAPER_LAMBDAS[0]])[0]
+        self.side = side
+
+    def crop(self, rng: np.random.Generator, H: int, W: int) -> np.ndarray:
+        y = int(rng.integers(0, self.side - H + 1))
+        x = int(rng.integers(0, self.side - W + 1))
+        return self.tex[y:y + H, x:x + W].copy()
+
+
+def serving_request_inputs(desc: dict, bank: TextureBank) -> Workload:
+    """Inputs of one serving request: config-3 scan rules, objects cropped from a texture
+    bank, Zernike probe modes (truth) and elliptical-aperture modes with a flat object as
+    the starting point (Section "Experimental setup")."""
+    F, J, L, M, seed = desc["F"], desc["J"], desc["L"], desc["M"], desc["seed"]
+    rng = np.random.default_rng(seed)
+    n_side = int(math.ceil(math.sqrt(J)))
+    step = int(round(0.1125 * F))
+    side = (n_side - 1) * step + F + 8
+    side = ((side + 15) // 16) * 16
+    lambdas = PAPER_LAMBDAS[0] * (1.0 + 0.05 * np.arange(L))
+    O = [bank.crop(rng, side, side) for _ in range(L)]
+    fwhm1 = 3.0 * F / 8.0
+    powers = list(0.5 ** np.arange(M))
+    P = np.stack([probe_modes(rng, F, M, fwhm1 * lambdas[0] / lambdas[l], powers, 1e5 / L) for l in range(L)])
+    offset = (side - ((n_side - 1) * step + F)) // 2
+    pos1 = raster_positions(rng, n_side, n_side, step, 2, offset)[:J]
+    pos = scale_positions(pos1, lambdas)
+    P0 = np.stack([elliptical_aperture_modes(F, M, photons=1e5 / L) for _ in range(L)])
+    O0 = [np.ones((side, side), np.complex128) for _ in range(L)]
+    return Workload(f"request{desc['index']}_F{F}_J{J}_L{L}_M{M}", F, L, M, J, [(side, side)] * L, O, P, O0, P0,
+                    pos, Geometry(lambdas, remap=True), loss="poisson", photons=1e5, seed=seed)
 
 
 def serving_workload(desc: dict) -> Workload:

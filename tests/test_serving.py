@@ -156,3 +156,38 @@ def test_plain_step_matches_fused_step(F):
     assert rel(O2.cpu().numpy(), O1.cpu().numpy()) < 1e-2
     assert rel(P2.cpu().numpy(), P1.cpu().numpy()) < 1e-2
     plan.close()
+
+
+@pytest.mark.gpu
+def test_reused_slot_runs_the_new_site():
+    """A released slot re-filled by another site, with the active slot set unchanged
+    ({0, 1} before and after): the tick must run the new site's graph."""
+    from paper_2311_14780_gb300.serve import Server
+    dev = torch.device("cuda", 0)
+    b_alone = _request(128, 1, 2, 3, 48, dev, iterations=3)
+    sv = Server(8 << 30)
+    s = sv.admit(b_alone)
+    while sv.tick():
+        pass
+    torch.cuda.synchronize()
+    sv.release(s)
+    sv.close()
+
+    a = _request(64, 1, 1, 3, 47, dev, iterations=2)
+    c = _request(64, 2, 2, 3, 49, dev, iterations=6)
+    b = _request(128, 1, 2, 3, 48, dev, iterations=3)
+    sv = Server(8 << 30)
+    sa, sc = sv.admit(a), sv.admit(c)
+    assert (sa, sc) == (0, 1)
+    assert sv.tick() == 2 and sv.tick() == 2     # a is done after two ticks
+    sv.release(sa)
+    sb = sv.admit(b)
+    assert sb == 0                              # same slot, same active set {0, 1}
+    while sv.tick():
+        pass
+    torch.cuda.synchronize()
+    assert sv.status(sb)[0] == 3
+    sv.release(sb)
+    sv.release(sc)
+    sv.close()
+    assert torch.equal(b.O, b_alone.O) and torch.equal(b.P, b_alone.P)
