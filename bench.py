@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="config5: HBM budget of the server")
     ap.add_argument("--no-plain", action="store_true", help="config5: skip the plain one-site-at-a-time run")
     ap.add_argument("--plain", action="store_true", help="time the plain unfused step instead of the fused one")
+    ap.add_argument("--serving-requests", type=int, default=16,
+                    help="requests of the reduced serving stream appended to the default line (0 = none)")
     ap.add_argument("--tick-evals", type=int, default=32768,
                     help="config5: admit while the active sites' evaluations per tick stay within this (0 = no cap)")
     return ap.parse_args()
@@ -362,6 +364,24 @@ def run_ours(args, rank: int, world: int):
         cpu = {"value": v_cpu, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
                "sample": f"{n_pos} of {w.J} positions ({ev} evals, {dt:.1f} s): FP64 NumPy loss + gradient + Adam"}
 
+    serving = None
+    if world == 1 and args.serving_requests > 0 and args.config == "config2" and not args.plain:
+        from paper_2311_14780_gb300.serve import plain_stream, serve_stream
+        import copy
+        sargs = copy.copy(args)
+        sargs.requests = args.serving_requests
+        served, plain_reqs = serving_requests(sargs, dev)
+        s_sum = serve_stream(served, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None)
+        p_sum = plain_stream(plain_reqs)
+        p_sum["final_loss_rel_diff_max"] = max(abs(a.final_loss - b.final_loss) / max(abs(b.final_loss), 1e-300)
+                                               for a, b in zip(served, plain_reqs))
+        serving = {"stream": f"first {sargs.requests} requests of the config-5 stream (Poisson arrivals, mean 50 ms; "
+                             f"F in {{128,256,512}}, J 100-900, L 1-5, M 1-8; {args.iterations} iterations each); "
+                             "full stream: bench.py --config config5",
+                   "served": s_sum, "plain_one_site_at_a_time": p_sum,
+                   "served_over_plain": s_sum["evals_per_s"] / p_sum["evals_per_s"],
+                   "site_iteration_ms_p50": s_sum["iter_ms_p50"], "site_iteration_ms_p99": s_sum["iter_ms_p99"]}
+
     if rank == 0:
         cfg = workload_config(w, args.config)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -373,7 +393,8 @@ def run_ours(args, rank: int, world: int):
                 "config": cfg, "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
                 "roofline": roof, "step_flop_rate_tflops": step_flops / (t_ms / args.steps / 1e3) / 1e12,
                 "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-                "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99))}
+                "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
+                "serving": serving}
         print(json.dumps(line))
     plan.close()
     if dist:

@@ -28,7 +28,7 @@ namespace ptycho {
 constexpr int kMaxL = 16;
 constexpr int kLossThreads = 256;
 constexpr int kTile = 32;        // object-gradient tile side
-constexpr int kMaxB = 128;       // positions per batch (upper bound; <= threads of the staging blocks)
+constexpr int kMaxB = 512;       // positions per batch (upper bound)
 
 struct KArgs {
   int L, M, F, J;
@@ -61,17 +61,17 @@ __device__ __forceinline__ int batch_pos(const KArgs& a, int i) {
 }
 
 // Scan positions (row, col) of the current batch for wavelength l and their power
-// coefficients, staged in shared memory by the first nb threads; invalid entries become
-// (-1, -1).  Ends with a block barrier.
+// coefficients, staged in shared memory (block-strided); invalid entries become (-1, -1).
+// Ends with a block barrier.
 __device__ __forceinline__ void stage_batch(const KArgs& a, int l, int2* spos, float* ssig) {
-  if ((int)threadIdx.x < a.nb) {
-    const int j = batch_pos(a, a.batch_off + threadIdx.x);
+  for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
+    const int j = batch_pos(a, a.batch_off + b);
     if (j < 0) {
-      spos[threadIdx.x] = make_int2(-1, -1);
-      ssig[threadIdx.x] = 0.f;
+      spos[b] = make_int2(-1, -1);
+      ssig[b] = 0.f;
     } else {
-      spos[threadIdx.x] = make_int2(a.pos[(l * a.J + j) * 2], a.pos[(l * a.J + j) * 2 + 1]);
-      ssig[threadIdx.x] = a.sigma ? __ldg(a.sigma + j) : 1.0f;
+      spos[b] = make_int2(a.pos[(l * a.J + j) * 2], a.pos[(l * a.J + j) * 2 + 1]);
+      ssig[b] = a.sigma ? __ldg(a.sigma + j) : 1.0f;
     }
   }
   __syncthreads();

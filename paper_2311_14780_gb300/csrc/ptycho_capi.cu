@@ -66,6 +66,7 @@ namespace {
 
 constexpr long long kMaxScratch = 2ll << 30;   // default upper bound of the FFT scratch
 constexpr long long kBatchEvals = 128;         // evaluations per batch the default aims for
+constexpr long long kBatchRows = 32768;        // and at least this many 1D FFT rows per pass
 constexpr double kPi = 3.14159265358979323846;
 
 bool supported_F(int F) { return F == 64 || F == 128 || F == 256 || F == 512; }
@@ -250,7 +251,8 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   // mode, no recompute) with B chosen so that one launch carries about kBatchEvals
   // evaluations; a small scratch stays in L2, a large one spills to HBM, which costs less than
   // launching small batches.  Only when one position's fields exceed the budget are the modes
-  // split into chunks that the adjoint recomputes.  An explicit scratch_bytes fits as many
+  // split into chunks that the adjoint recomputes (small-mode problems also get at least
+  // kBatchRows FFT rows per pass).  An explicit scratch_bytes fits as many
   // positions as the budget holds.
   const long long FF8 = (long long)F * F * (long long)sizeof(float2);
   const long long LM = (long long)g->L * g->M;
@@ -260,7 +262,8 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     p->C = (int)LM;
     p->nchunks = 1;
     long long B = p->scratch_budget / (LM * FF8);
-    if (g->scratch_bytes <= 0) B = std::min<long long>(B, (kBatchEvals + LM - 1) / LM);
+    if (g->scratch_bytes <= 0)
+      B = std::min<long long>(B, std::max((kBatchEvals + LM - 1) / LM, (kBatchRows + LM * F - 1) / (LM * F)));
     p->B = (int)std::max<long long>(1, std::min<long long>(B, ptycho::kMaxB));
     p->B = std::min(p->B, g->J);
   } else {
