@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scratch-mb", type=int, default=0, help="L2 scratch budget of the plan (0 = library default)")
+    ap.add_argument("--overlap", type=int, default=0, help="position batches in flight (0 = library default)")
     ap.add_argument("--requests", type=int, default=64, help="config5: number of serving requests")
     ap.add_argument("--iterations", type=int, default=20, help="config5: iterations per request")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="config5: HBM budget of the server")
@@ -252,7 +253,7 @@ def run_ours(args, rank: int, world: int):
     plan_true.close()
     Ih = syn.poisson_measure(I_clean, 1234 + rank)
     eps = syn.default_eps(Ih)
-    plan = plan_for(w, eps=eps, scratch_bytes=args.scratch_mb << 20)
+    plan = plan_for(w, eps=eps, scratch_bytes=args.scratch_mb << 20, overlap=args.overlap)
     O = pack_objects(w.O0, dev)
     P = torch.as_tensor(w.P0, dtype=torch.complex64, device=dev).contiguous()
     Im = torch.as_tensor(Ih, device=dev).contiguous()

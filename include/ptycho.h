@@ -75,6 +75,8 @@ typedef struct {
   float eps;                /* intensity floor added to I in the loss and its gradient  */
   int64_t scratch_bytes;    /* FFT scratch budget in bytes; 0 = library default (about 128
                                evaluations per batch, at most 2 GiB)                  */
+  int32_t overlap;          /* position batches in flight on separate streams (1..4), each
+                               with its own scratch set; 0 = library default (2)       */
 } ptycho_geom_t;
 
 /* Adam state (Kingma & Ba), cited by the paper as its optimiser.  Real and imaginary

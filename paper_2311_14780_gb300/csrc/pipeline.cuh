@@ -88,8 +88,26 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const int LM = p.L * p.M;
   const dim3 row_blk(RowCfg<F>::threads), col_blk(ColCfg<F>::threads);
   const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
+  const int nbatches = (c.nbatch + p.B - 1) / p.B;
+  const int nsets = p.nsets < nbatches ? p.nsets : nbatches;
+  const long long set_S = (long long)p.B * p.C * FF, set_I = (long long)p.B * p.G * FF, set_F = (long long)p.B * FF;
+  cudaStream_t streams[ptycho_plan::kMaxSets] = {st};
+  for (int i = 1; i < nsets; ++i) streams[i] = p.side[i - 1];
+  if (nsets > 1) {                                    // the side streams follow the caller's work so far
+    if (cudaEventRecord(p.ev_fork, st) != cudaSuccess) return PTYCHO_ECUDA;
+    for (int i = 1; i < nsets; ++i)
+      if (cudaStreamWaitEvent(streams[i], p.ev_fork, 0) != cudaSuccess) return PTYCHO_ECUDA;
+  }
 
-  for (int off = 0; off < c.nbatch; off += p.B) {
+  for (int k = 0, off = 0; off < c.nbatch; ++k, off += p.B) {
+    const int set = k % nsets;
+    cudaStream_t cs = streams[set];
+    float2* S = p.d_S + set * set_S;
+    float* Ip = p.d_Ipart + set * set_I;
+    la.Ipart = Ip;
+    la.D = grad ? p.d_D + set * set_F : nullptr;
+    aa.D = p.d_D + set * set_F;
+    aa.Gt = p.d_Gt ? p.d_Gt + set * set_F : nullptr;
     a.batch_off = off;
     a.nb = (c.nbatch - off < p.B) ? (c.nbatch - off) : p.B;
     // region of each object the batch's patches cover (exact for the identity order, else
@@ -100,8 +118,8 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       if (identity) {
         y0 = x0 = 1 << 30;
         y1 = x1 = -1;
-        for (int k = off; k < off + a.nb; ++k) {
-          const int y = p.pos_host[((size_t)l * p.J + k) * 2], x = p.pos_host[((size_t)l * p.J + k) * 2 + 1];
+        for (int q = off; q < off + a.nb; ++q) {
+          const int y = p.pos_host[((size_t)l * p.J + q) * 2], x = p.pos_host[((size_t)l * p.J + q) * 2 + 1];
           y0 = y < y0 ? y : y0; x0 = x < x0 ? x : x0;
           y1 = y + F > y1 ? y + F : y1; x1 = x + F > x1 ? x + F : x1;
         }
@@ -114,39 +132,49 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
-      PTY_LAUNCH(p, kRowFwd, st,
-                 k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, st>>>(
-                     c.O, c.P, p.d_S, a));
+      PTY_LAUNCH(p, kRowFwd, cs,
+                 k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs>>>(c.O, c.P, S, a));
       if (store)
-        PTY_LAUNCH(p, kColFwd, st,
-                   k_col_fwd<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, st>>>(
-                       p.d_S, p.d_Ipart, a, ch == 0));
+        PTY_LAUNCH(p, kColFwd, cs,
+                   k_col_fwd<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs>>>(
+                       S, Ip, a, ch == 0));
       else
-        PTY_LAUNCH(p, kColFwd, st,
-                   k_col_fwd<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, st>>>(
-                       p.d_S, p.d_Ipart, a, ch == 0));
+        PTY_LAUNCH(p, kColFwd, cs,
+                   k_col_fwd<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs>>>(
+                       S, Ip, a, ch == 0));
     }
-    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, st>>>(a, la));
+    PTY_LAUNCH(p, kLoss, cs, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, cs>>>(a, la));
     if (!grad) continue;
-    if (p.remap) PTY_LAUNCH(p, kRemapAdj, st, k_remap_adj<F><<<dim3(FF / 256, a.nb), 256, 0, st>>>(a, aa));
+    if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, k_remap_adj<F><<<dim3(FF / 256, a.nb), 256, 0, cs>>>(a, aa));
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       if (store) {
-        PTY_LAUNCH(p, kColAdj, st,
-                   k_col_adj<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
+        PTY_LAUNCH(p, kColAdj, cs,
+                   k_col_adj<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs>>>(S, a, aa));
       } else {
-        PTY_LAUNCH(p, kRowFwd, st,
-                   k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, st>>>(
-                       c.O, c.P, p.d_S, a));
-        PTY_LAUNCH(p, kColAdj, st,
-                   k_col_adj<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, st>>>(p.d_S, a, aa));
+        PTY_LAUNCH(p, kRowFwd, cs,
+                   k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs>>>(c.O, c.P, S, a));
+        PTY_LAUNCH(p, kColAdj, cs,
+                   k_col_adj<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs>>>(S, a, aa));
       }
-      PTY_LAUNCH(p, kRowAdj, st,
+      // the probe and object gradients accumulate in batch order across the two streams
+      if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_radj[(k - 1) % nsets], 0) != cudaSuccess)
+        return PTYCHO_ECUDA;
+      PTY_LAUNCH(p, kRowAdj, cs,
                  k_row_adj<F><<<dim3(F / RowAdjCfg<F>::RPB, a.chunk_len), RowAdjCfg<F>::threads, RowAdjCfg<F>::smem,
-                                st>>>(c.O, c.P, p.d_S, c.gP, a));
-      PTY_LAUNCH(p, kObjGrad, st, k_obj_grad<F><<<dim3(max_tiles, p.L), 256, 0, st>>>(p.d_S, c.gO, a));
+                                cs>>>(c.O, c.P, S, c.gP, a));
+      if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+      if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_og[(k - 1) % nsets], 0) != cudaSuccess)
+        return PTYCHO_ECUDA;
+      PTY_LAUNCH(p, kObjGrad, cs, k_obj_grad<F><<<dim3(max_tiles, p.L), 256, 0, cs>>>(S, c.gO, a));
+      if (nsets > 1 && cudaEventRecord(p.ev_og[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
     }
+  }
+  for (int i = 1; i < nsets; ++i) {                   // join the side streams back
+    if (cudaEventRecord(p.ev_join[i - 1], streams[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(st, p.ev_join[i - 1], 0) != cudaSuccess)
+      return PTYCHO_ECUDA;
   }
   if (need_loss) {
     double* out = c.loss;

@@ -24,6 +24,17 @@ struct ptycho_plan {
   int store = 1, B = 1, C = 1, nchunks = 1, G = 1, MG = 1;
   long long scratch_budget = 0;
 
+  // nsets buffer sets let consecutive position batches overlap: batch k runs on stream
+  // k % nsets (the caller's stream, then side[0..]) with buffer set k % nsets; events keep the
+  // probe- and object-gradient accumulations in batch order
+  static constexpr int kMaxSets = 4;
+  int nsets = 1;
+  cudaStream_t side[kMaxSets - 1] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxSets - 1] = {};
+  cudaEvent_t ev_radj[kMaxSets] = {};
+  cudaEvent_t ev_og[kMaxSets] = {};
+
   // device workspace (all owned by the plan)
   int32_t* d_pos = nullptr;
   int32_t* d_ident = nullptr;
@@ -33,10 +44,10 @@ struct ptycho_plan {
   int32_t* d_rt_ptr = nullptr;
   int32_t* d_rt_idx = nullptr;
   float* d_rt_w = nullptr;
-  float2* d_S = nullptr;
-  float* d_Ipart = nullptr;
-  float* d_D = nullptr;
-  float* d_Gt = nullptr;                       // R^T D per batch position (remap only)
+  float2* d_S = nullptr;                       // [nsets][B][C][F][F]
+  float* d_Ipart = nullptr;                    // [nsets][B][G][F][F]
+  float* d_D = nullptr;                        // [nsets][B][F][F]
+  float* d_Gt = nullptr;                       // [nsets][B][F][F] R^T D (remap only)
   double* d_loss_part = nullptr;
   float2* d_gO = nullptr;
   float2* d_gP = nullptr;

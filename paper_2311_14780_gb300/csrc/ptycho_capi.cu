@@ -67,6 +67,7 @@ namespace {
 constexpr long long kMaxScratch = 2ll << 30;   // default upper bound of the FFT scratch
 constexpr long long kBatchEvals = 128;         // evaluations per batch the default aims for
 constexpr long long kBatchRows = 32768;        // and at least this many 1D FFT rows per pass
+constexpr int kDefaultOverlap = 2;             // position batches in flight
 constexpr double kPi = 3.14159265358979323846;
 
 bool supported_F(int F) { return F == 64 || F == 128 || F == 256 || F == 512; }
@@ -93,6 +94,15 @@ int upload(T* dst, const T* src, long long count) {
 
 void free_plan(ptycho_plan* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  for (int i = 0; i < ptycho_plan::kMaxSets; ++i) {
+    if (p->ev_radj[i]) cudaEventDestroy(p->ev_radj[i]);
+    if (p->ev_og[i]) cudaEventDestroy(p->ev_og[i]);
+    if (i < ptycho_plan::kMaxSets - 1) {
+      if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
+      if (p->side[i]) cudaStreamDestroy(p->side[i]);
+    }
+  }
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status};
   for (void* q : ptrs)
@@ -290,9 +300,25 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   rc = rc ? rc : dalloc(p, &p->d_pos, (long long)g->L * g->J * 2);
   rc = rc ? rc : dalloc(p, &p->d_ident, g->J);
   rc = rc ? rc : dalloc(p, &p->d_tw, F);
-  rc = rc ? rc : dalloc(p, &p->d_S, (long long)p->B * p->C * FF);
-  rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->B * p->G * FF);
-  rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->B * FF);
+  // overlap consecutive batches (several buffer sets) when the fields are kept between passes
+  {
+    const int want = g->overlap > 0 ? std::min(g->overlap, ptycho_plan::kMaxSets) : kDefaultOverlap;
+    const int nbat = (g->J + p->B - 1) / p->B;
+    p->nsets = p->store ? std::max(1, std::min(want, nbat)) : 1;
+  }
+  if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = PTYCHO_ECUDA;
+  for (int i = 0; i < p->nsets && !rc; ++i) {
+    if (cudaEventCreateWithFlags(&p->ev_radj[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_og[i], cudaEventDisableTiming) != cudaSuccess)
+      rc = PTYCHO_ECUDA;
+    if (i > 0 && !rc &&
+        (cudaStreamCreateWithFlags(&p->side[i - 1], cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&p->ev_join[i - 1], cudaEventDisableTiming) != cudaSuccess))
+      rc = PTYCHO_ECUDA;
+  }
+  rc = rc ? rc : dalloc(p, &p->d_S, (long long)p->nsets * p->B * p->C * FF);
+  rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->nsets * p->B * p->G * FF);
+  rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->nsets * p->B * FF);
   rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / ptycho::kLossThreads));
   rc = rc ? rc : dalloc(p, &p->d_gO, p->O_numel);
   rc = rc ? rc : dalloc(p, &p->d_gP, p->P_numel);
@@ -324,7 +350,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     std::vector<float2> w;
     std::vector<float> rt_w;
     build_remap(F, g->z, g->det_pixel, g->tilt_rad, base, w, rt_ptr, rt_idx, rt_w);
-    rc = rc ? rc : dalloc(p, &p->d_Gt, (long long)p->B * FF);
+    rc = rc ? rc : dalloc(p, &p->d_Gt, (long long)p->nsets * p->B * FF);
     rc = rc ? rc : dalloc(p, &p->d_tap_base, FF);
     rc = rc ? rc : dalloc(p, &p->d_tap_w, FF);
     rc = rc ? rc : dalloc(p, &p->d_rt_ptr, FF + 1);
