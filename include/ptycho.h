@@ -88,6 +88,10 @@ typedef struct {
   int32_t t;                /* steps taken so far; ptycho_step increments it            */
   float* mO; float* vO;     /* [2 * numel(O)]                                           */
   float* mP; float* vP;     /* [2 * numel(P)]                                           */
+  int32_t* t_dev;           /* optional DEVICE step counter (zero-initialised): when set,
+                               ptycho_step increments it on the device and the bias
+                               correction reads it there, so a captured CUDA graph of
+                               ptycho_step can be replayed; t is then left unchanged  */
 } ptycho_adam_t;
 
 /* Validates the geometry and every scan position (PTYCHO_ERANGE names an out-of-object

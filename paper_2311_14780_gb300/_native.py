@@ -30,6 +30,7 @@ class Adam(ctypes.Structure):
         ("lr_O", ctypes.c_float), ("lr_P", ctypes.c_float), ("beta1", ctypes.c_float),
         ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("t", ctypes.c_int32),
         ("mO", ctypes.c_void_p), ("vO", ctypes.c_void_p), ("mP", ctypes.c_void_p), ("vP", ctypes.c_void_p),
+        ("t_dev", ctypes.c_void_p),
     ]
 
 

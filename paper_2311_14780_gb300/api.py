@@ -267,8 +267,10 @@ class AdamState:
     """Adam moments for O and P (device tensors, 2 floats per complex element)."""
 
     def __init__(self, plan: Plan, lr_O: float, lr_P: float, beta1: float = 0.9, beta2: float = 0.999,
-                 eps: float = 1e-8):
+                 eps: float = 1e-8, device_counter: bool = False):
         dev = plan.device
+        # with a device step counter a captured CUDA graph of Plan.step can be replayed
+        self.t_dev = torch.zeros(1, dtype=torch.int32, device=dev) if device_counter else None
         self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps = lr_O, lr_P, beta1, beta2, eps
         self.t = 0
         self.mO = torch.zeros(2 * plan.numel_O, dtype=torch.float32, device=dev)
@@ -281,6 +283,7 @@ class AdamState:
         s.lr_O, s.lr_P, s.beta1, s.beta2, s.eps, s.t = self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps, self.t
         s.mO, s.vO = self.mO.data_ptr(), self.vO.data_ptr()
         s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
+        s.t_dev = None if self.t_dev is None else self.t_dev.data_ptr()
         return s
 
 

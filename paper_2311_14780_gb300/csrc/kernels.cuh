@@ -486,6 +486,10 @@ k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
 // loss reduction and Adam (defined in ptycho_capi.cu)
 // ---------------------------------------------------------------------------------------
 __global__ void k_loss_reduce(const double* __restrict__ part, long long n, double* out);
+__global__ void k_tick(int* t);
+__global__ void k_adam_dev(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m,
+                           float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                           const int* __restrict__ t_dev);
 __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m,
                        float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
                        float c2);

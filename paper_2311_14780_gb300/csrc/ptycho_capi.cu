@@ -38,6 +38,29 @@ k_adam(float* __restrict__ theta, const float* __restrict__ grad, float* __restr
   }
 }
 
+// step counter += 1 (one thread): the Adam bias correction of a replayed graph reads it
+__global__ void k_tick(int* t) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
+}
+
+// Adam with the step counter read on the device (for graph replays).
+__global__ void __launch_bounds__(256)
+k_adam_dev(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
+           long long n, float lr, float b1, float b2, float eps, const int* __restrict__ t_dev) {
+  const float t = (float)(*t_dev);
+  const float c1 = 1.0f / (1.0f - powf(b1, t));
+  const float c2 = 1.0f / (1.0f - powf(b2, t));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float g = grad[i];
+    const float mi = fmaf(b1, m[i], (1.f - b1) * g);
+    const float vi = fmaf(b2, v[i], (1.f - b2) * g * g);
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st) {
   if (!p.prof) return -1;
   const size_t i = p.ev_used;
@@ -487,12 +510,27 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, const fl
   int rc = ptycho_adjoint(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
                           reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP), loss_dev, stream);
   if (rc) return rc;
-  s->t += 1;
-  const double c1 = 1.0 / (1.0 - pow((double)s->beta1, (double)s->t));
-  const double c2 = 1.0 / (1.0 - pow((double)s->beta2, (double)s->t));
   cudaStream_t st = (cudaStream_t)stream;
   const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;
   const int grid = 4 * p->sms;
+  if (s->t_dev) {
+    // device step counter: the update can be captured once and replayed
+    ptycho::k_tick<<<1, 32, 0, st>>>(s->t_dev);
+    ++p->last_launches;
+    if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
+    long long ev = ptycho::prof_begin(*p, ptycho::kAdam, st);
+    ptycho::k_adam_dev<<<grid, 256, 0, st>>>(O, reinterpret_cast<const float*>(p->d_gO), s->mO, s->vO, nO, s->lr_O,
+                                             s->beta1, s->beta2, s->eps, s->t_dev);
+    ptycho::k_adam_dev<<<grid, 256, 0, st>>>(P, reinterpret_cast<const float*>(p->d_gP), s->mP, s->vP, nP, s->lr_P,
+                                             s->beta1, s->beta2, s->eps, s->t_dev);
+    p->last_launches += 2;
+    if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
+    ptycho::prof_end(*p, ev, st);
+    return PTYCHO_OK;
+  }
+  s->t += 1;
+  const double c1 = 1.0 / (1.0 - pow((double)s->beta1, (double)s->t));
+  const double c2 = 1.0 / (1.0 - pow((double)s->beta2, (double)s->t));
   long long ev = ptycho::prof_begin(*p, ptycho::kAdam, st);
   ptycho::k_adam<<<grid, 256, 0, st>>>(O, reinterpret_cast<const float*>(p->d_gO), s->mO, s->vO, nO, s->lr_O,
                                        s->beta1, s->beta2, s->eps, (float)c1, (float)c2);

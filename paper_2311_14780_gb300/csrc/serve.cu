@@ -17,31 +17,6 @@
 
 #include "plan.h"
 
-namespace ptycho {
-
-// step counter += 1 (one thread): the Adam bias correction of a replayed graph reads it
-__global__ void k_tick(int* t) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
-}
-
-// Adam with the step counter read on the device (for graph replays).
-__global__ void __launch_bounds__(256)
-k_adam_dev(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
-           long long n, float lr, float b1, float b2, float eps, const int* __restrict__ t_dev) {
-  const float t = (float)(*t_dev);
-  const float c1 = 1.0f / (1.0f - powf(b1, t));
-  const float c2 = 1.0f / (1.0f - powf(b2, t));
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float g = grad[i];
-    const float mi = fmaf(b1, m[i], (1.f - b1) * g);
-    const float vi = fmaf(b2, v[i], (1.f - b2) * g * g);
-    m[i] = mi;
-    v[i] = vi;
-    theta[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-  }
-}
-
-}  // namespace ptycho
 
 namespace {
 

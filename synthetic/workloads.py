@@ -210,12 +210,14 @@ def object_smooth(rng: np.random.Generator, H: int, W: int, sigma: float = 3.0) 
 def _rectangles(rng: np.random.Generator, H: int, W: int, lo: int, hi: int, cover: float):
     rects = []
     occ = np.zeros((H, W), bool)
-    while occ.mean() < cover:
+    covered, target = 0, cover * H * W
+    while covered < target:
         h = int(rng.integers(lo, hi + 1))
         w = int(rng.integers(lo, hi + 1))
         y = int(rng.integers(0, H - h + 1))
         x = int(rng.integers(0, W - w + 1))
         rects.append((y, x, h, w))
+        covered += int(h * w - np.count_nonzero(occ[y:y + h, x:x + w]))
         occ[y:y + h, x:x + w] = True
     return rects
 

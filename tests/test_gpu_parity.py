@@ -269,3 +269,50 @@ def test_deterministic_repeat(dev):
     b = plan.adjoint(case.O, case.P, case.Im)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
     plan.close()
+
+
+def _sampled_full_size(dev, w, n_frames, n_grad, seed):
+    """Full-size plan; predicted frames of a sample and the gradient of a smaller subset
+    checked against the oracle, at a near-truth evaluation point."""
+    from paper_2311_14780_gb300 import pack_objects, plan_for
+    taps = orc.remap_taps(w.F, w.geom.z, w.geom.det_pixel, w.geom.tilt_rad) if w.geom.remap else None
+    rng = np.random.default_rng(seed)
+    frames = sorted(rng.choice(w.J, size=n_frames, replace=False).tolist())
+    gframes = frames[:n_grad]
+    O_e, P_e = syn.near_truth(w, seed=seed)
+    O0 = [as_c64_roundtrip(o) for o in O_e]
+    P0 = as_c64_roundtrip(P_e)
+    clean = np.zeros((w.J, w.F, w.F))
+    clean[gframes] = orc.predict(w.O_true, w.P_true, w.pos, None, None, taps, frames=gframes)
+    Ih = syn.poisson_measure(clean, seed)
+    eps = 1e-9 * float(Ih[gframes].mean())
+    plan = plan_for(w, eps=eps)
+    O = pack_objects(O0, dev)
+    P = c64(P0, dev)
+    Ip = plan.forward(O, P).cpu().numpy()
+    Ir = orc.predict(O0, P0, w.pos, None, None, taps, frames=frames)
+    bt = torch.as_tensor(np.asarray(gframes, np.int32), device=dev)
+    La, gO, gP = plan.adjoint(O, P, torch.as_tensor(Ih, device=dev).contiguous(), batch=bt)
+    Lr, gOr, gPr = orc.gradient(O0, P0, w.pos, Ih, w.loss, eps, None, None, None, taps, frames=gframes)
+    gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    err = dict(I=rel(Ip[frames], Ir), L=abs(float(La.item()) - Lr) / abs(Lr), La=0.0,
+               gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr))
+    plan.close()
+    return err
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("F,M,L", [(128, 1, 1), (128, 8, 5), (256, 4, 3), (256, 1, 5), (512, 4, 3), (512, 8, 1)])
+def test_config3_points_full_size_sampled(dev, F, M, L):
+    """Throughput-sweep points (400 positions, 70 % overlap, rectangle objects, remap,
+    Poisson) at full size: sampled frames and a position subset's gradient."""
+    w = syn.config3(F, M, L)
+    assert_ok(_sampled_full_size(dev, w, n_frames=3, n_grad=2, seed=F + M + L))
+
+
+@pytest.mark.slow
+def test_config4_full_size_sampled(dev):
+    """~200M-parameter case (6 wavelengths x 10 modes of 512^2, 6 objects of 3584^2, 900
+    positions): sampled frames and the gradient of one position against the oracle."""
+    w = syn.config4()
+    assert_ok(_sampled_full_size(dev, w, n_frames=2, n_grad=1, seed=4))

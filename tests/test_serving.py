@@ -191,3 +191,32 @@ def test_reused_slot_runs_the_new_site():
     sv.release(sc)
     sv.close()
     assert torch.equal(b.O, b_alone.O) and torch.equal(b.P, b_alone.P)
+
+
+@pytest.mark.gpu
+def test_graph_replayed_steps_match_eager_steps():
+    """ptycho_step with a device step counter, captured once as a CUDA graph and replayed,
+    gives the same parameters as eager steps with the host counter."""
+    from paper_2311_14780_gb300 import AdamState
+    from paper_2311_14780_gb300.api import plan_geometry_plan
+    dev = torch.device("cuda", 0)
+    r = _request(128, 2, 2, 4, 50, dev)
+    plan = plan_geometry_plan(r)
+    O1, P1 = r.O.clone(), r.P.clone()
+    O2, P2 = r.O.clone(), r.P.clone()
+    s1 = AdamState(plan, 1e-2, 1e-2)
+    s2 = AdamState(plan, 1e-2, 1e-2, device_counter=True)
+    l2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        plan.step(s1, O1, P1, r.I_meas)
+    plan.step(s2, O2, P2, r.I_meas, loss_out=l2)          # first step eagerly (warms up)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.step(s2, O2, P2, r.I_meas, loss_out=l2)
+    g.replay()                                              # step 2 (capturing ran nothing)
+    g.replay()                                              # step 3
+    torch.cuda.synchronize()
+    assert int(s2.t_dev.item()) == 3
+    assert rel(O2.cpu().numpy(), O1.cpu().numpy()) < REL
+    assert rel(P2.cpu().numpy(), P1.cpu().numpy()) < REL
+    plan.close()
