@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--scratch-mb", type=int, default=0, help="L2 scratch budget of the plan (0 = library default)")
     ap.add_argument("--overlap", type=int, default=0, help="position batches in flight (0 = library default)")
     ap.add_argument("--graph", action="store_true", help="replay one step captured as a CUDA graph")
+    ap.add_argument("--flags", type=int, default=0, help="PTYCHO_FLAG_* pipeline variants")
+    ap.add_argument("--col-groups", type=int, default=0, help="mode groups of the column passes (0 = default)")
     ap.add_argument("--requests", type=int, default=64, help="config5: number of serving requests")
     ap.add_argument("--iterations", type=int, default=20, help="config5: iterations per request")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="config5: HBM budget of the server")
@@ -254,7 +256,8 @@ def run_ours(args, rank: int, world: int):
     plan_true.close()
     Ih = syn.poisson_measure(I_clean, 1234 + rank)
     eps = syn.default_eps(Ih)
-    plan = plan_for(w, eps=eps, scratch_bytes=args.scratch_mb << 20, overlap=args.overlap)
+    plan = plan_for(w, eps=eps, scratch_bytes=args.scratch_mb << 20, overlap=args.overlap, flags=args.flags,
+                    col_groups=args.col_groups)
     O = pack_objects(w.O0, dev)
     P = torch.as_tensor(w.P0, dtype=torch.complex64, device=dev).contiguous()
     Im = torch.as_tensor(Ih, device=dev).contiguous()

@@ -50,6 +50,18 @@ extern "C" {
 #define PTYCHO_ETOOLARGE (-7)    /* problem does not fit ptycho_forward_noalloc's array */
 #define PTYCHO_EBUSY (-8)        /* serving: no free slot, or the HBM budget is exhausted  */
 
+/* Pipeline variants (ptycho_geom_t.flags).  All give the same results up to FP32 rounding.
+ * RECOMPUTE_COLUMNS: the adjoint recomputes the column DFT from the kept row-pass output
+ *   instead of keeping Psi (less memory traffic, one more 1D pass per evaluation); the
+ *   default for F >= 256, where it measured faster.
+ * KEEP_PSI: keep Psi between the passes (the default for F < 256).
+ * OBJ_GRAD_ATOMIC: the row adjoint adds the object gradient with FP32 atomics instead of
+ *   the tile-owned gather (faster; the summation order, and so the last bits of grad O,
+ *   then vary between runs). */
+#define PTYCHO_FLAG_RECOMPUTE_COLUMNS 1
+#define PTYCHO_FLAG_OBJ_GRAD_ATOMIC 2
+#define PTYCHO_FLAG_KEEP_PSI 4
+
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */
 
@@ -77,6 +89,9 @@ typedef struct {
                                evaluations per batch, at most 2 GiB)                  */
   int32_t overlap;          /* position batches in flight on separate streams (1..4), each
                                with its own scratch set; 0 = library default (2)       */
+  int32_t flags;            /* PTYCHO_FLAG_* variants; 0 = defaults                      */
+  int32_t col_groups;       /* mode groups of the column passes (partial intensity sums
+                               per position); 0 = library default                       */
 } ptycho_geom_t;
 
 /* Adam state (Kingma & Ba), cited by the paper as its optimiser.  Real and imaginary

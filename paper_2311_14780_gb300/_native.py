@@ -21,7 +21,8 @@ class Geom(ctypes.Structure):
         ("obj_h", c_int32_p), ("obj_w", c_int32_p), ("pos", c_int32_p), ("lam", c_double_p),
         ("z", ctypes.c_double), ("det_pixel", ctypes.c_double), ("tilt_rad", ctypes.c_double),
         ("remap", ctypes.c_int32), ("loss", ctypes.c_int32), ("eps", ctypes.c_float),
-        ("scratch_bytes", ctypes.c_int64), ("overlap", ctypes.c_int32),
+        ("scratch_bytes", ctypes.c_int64), ("overlap", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("col_groups", ctypes.c_int32),
     ]
 
 

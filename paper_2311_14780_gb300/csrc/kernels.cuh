@@ -50,6 +50,14 @@ struct KArgs {
                                  // the batch's patches (the whole object when not known on the host)
 };
 
+// Programmatic dependent launch: the pipeline launches each kernel so that it may start
+// while the previous kernel of its stream finishes.  pdl_wait() blocks until that kernel
+// has completed and its writes are visible (a no-op for an ordinary launch); every pipeline
+// kernel calls it before touching global memory.  pdl_trigger() lets the next kernel start
+// launching its blocks.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // Position index of batch entry i, or -1 (and the status bit set) if out of range.
 __device__ __forceinline__ int batch_pos(const KArgs& a, int i) {
   const int j = a.bidx[i];
@@ -99,6 +107,8 @@ __device__ __forceinline__ float sigma_of(const KArgs& a, int j) { return a.sigm
 template <int F>
 __global__ void __launch_bounds__(RowCfg<F>::threads)
 k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowCfg<F>::T;
   extern __shared__ float2 smem[];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
@@ -133,6 +143,8 @@ k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
 k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % W, t = threadIdx.x / W;
@@ -214,6 +226,8 @@ __device__ __forceinline__ float poisson_term(float Ie, float Ih) {
 template <int F>
 __global__ void __launch_bounds__(kLossThreads)
 k_loss(KArgs a, LossArgs la) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int FF = F * F;
   __shared__ double red[kLossThreads / 32];
   const int b = blockIdx.y;
@@ -289,6 +303,8 @@ struct AdjArgs {
 template <int F>
 __global__ void __launch_bounds__(256)
 k_remap_adj(KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int FF = F * F;
   const int u = blockIdx.x * 256 + threadIdx.x;
   const int b = blockIdx.y;
@@ -305,6 +321,8 @@ k_remap_adj(KArgs a, AdjArgs aa) {
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
 k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
   extern __shared__ float2 smem[];
   float* gt = reinterpret_cast<float*>(smem + W * Xch<F>::region_cols);   // [F][W]
@@ -345,7 +363,8 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
 
 // ---------------------------------------------------------------------------------------
 // adjoint row pass: chi = dL/dpsi; probe gradient summed over the batch; object-gradient
-// contributions conj(sigma P) chi left in S.  The batch is split over kAdjSlots groups of
+// contributions conj(sigma P) chi left in S (or, with ATOMIC, added to grad O with FP32
+// atomics).  The batch is split over kAdjSlots groups of
 // warps (slot s takes positions s, s + kAdjSlots, ...); their probe-gradient sums are added
 // in slot order through shared memory, so the result does not depend on timing.
 // grid (F/RPB, chunk_len)
@@ -361,10 +380,12 @@ template <int F> struct RowAdjCfg {
   static constexpr int smem = smem_xch > smem_red ? smem_xch : smem_red;
 };
 
-template <int F>
-__global__ void __launch_bounds__(RowAdjCfg<F>::threads)
+template <int F, bool ATOMIC>
+__global__ void __launch_bounds__(RowAdjCfg<F>::threads, (F <= 256 ? 2 : 1))
 k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
-          float2* __restrict__ gP, KArgs a) {
+          float2* __restrict__ gP, float2* __restrict__ gO, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowAdjCfg<F>::T, RPB = RowAdjCfg<F>::RPB;
   extern __shared__ float2 smem[];
   __shared__ int2 spos[kMaxB];
@@ -379,12 +400,9 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   const float2* Prow = P + ((long long)mode * F + r) * F;
   const float2* Ol = O + a.obj_off[l];
   const int Wl = a.obj_w[l];
-  float2 pr[N2], acc[N2];
+  float2 acc[N2];
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) {
-    pr[n2] = __ldg(Prow + t + N1 * n2);
-    acc[n2] = make_float2(0.f, 0.f);
-  }
+  for (int n2 = 0; n2 < N2; ++n2) acc[n2] = make_float2(0.f, 0.f);
   for (int b = slot; b < a.nb; b += kAdjSlots) {
     const int2 yx = spos[b];
     if (yx.x < 0) continue;                           // uniform over the slot's warps
@@ -402,7 +420,11 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
       const float2 gp = cconjmul(p[n2], v[n2]);     // conj(p) chi
       acc[n2].x = fmaf(s, gp.x, acc[n2].x);
       acc[n2].y = fmaf(s, gp.y, acc[n2].y);
-      row[t + N1 * n2] = cscale(cconjmul(pr[n2], v[n2]), s);     // conj(sigma P) chi
+      const float2 go = cscale(cconjmul(__ldg(Prow + t + N1 * n2), v[n2]), s);   // conj(sigma P) chi
+      if (ATOMIC)
+        atomicAdd(gO + a.obj_off[l] + (long long)(yx.x + r) * Wl + yx.y + t + N1 * n2, go);
+      else
+        row[t + N1 * n2] = go;
     }
   }
   // slots 1.. hand their sums to slot 0 through shared memory (the exchange area is free now)
@@ -433,6 +455,8 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
 template <int F>
 __global__ void __launch_bounds__(256)
 k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int2 spos[kMaxB];
   __shared__ float ssig[kMaxB];
   const int l = blockIdx.y;

@@ -16,6 +16,22 @@ namespace ptycho {
     prof_end((p), pty_ev, (st));                                     \
   } while (0)
 
+// Launch with programmatic stream serialisation (see pdl_wait in kernels.cuh).
+template <typename... KP, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
+}
+
 template <int F>
 int prepare_kernels() {
   static int done = 0;
@@ -23,7 +39,8 @@ int prepare_kernels() {
   const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(k_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowAdjCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowAdjCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowAdjCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
@@ -40,7 +57,11 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   constexpr int FF = F * F;
   const bool grad = c.kind == CallKind::Adjoint;
   const bool need_loss = c.kind != CallKind::Forward;
-  const bool store = grad && p.store;   // keep Psi only when an adjoint follows
+  // keep Psi between the passes only when an adjoint follows and the variant asks for it;
+  // otherwise the adjoint recomputes the column DFT from the kept row-pass output
+  const bool store = grad && p.store && !(p.flags & PTYCHO_FLAG_RECOMPUTE_COLUMNS);
+  const bool rerun_rows = !p.store;     // modes in chunks: the row pass is rerun as well
+  const bool obj_atomic = (p.flags & PTYCHO_FLAG_OBJ_GRAD_ATOMIC) != 0;
 
   KArgs a{};
   a.L = p.L; a.M = p.M; a.F = F; a.J = p.J;
@@ -133,41 +154,46 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       PTY_LAUNCH(p, kRowFwd, cs,
-                 k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs>>>(c.O, c.P, S, a));
+                 launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
       if (store)
         PTY_LAUNCH(p, kColFwd, cs,
-                   k_col_fwd<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs>>>(
+                   launch_pdl(k_col_fwd<F, true>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs, 
                        S, Ip, a, ch == 0));
       else
         PTY_LAUNCH(p, kColFwd, cs,
-                   k_col_fwd<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs>>>(
+                   launch_pdl(k_col_fwd<F, false>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs, 
                        S, Ip, a, ch == 0));
     }
-    PTY_LAUNCH(p, kLoss, cs, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, cs>>>(a, la));
+    PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(FF / kLossThreads, a.nb), kLossThreads, 0, cs, a, la));
     if (!grad) continue;
-    if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, k_remap_adj<F><<<dim3(FF / 256, a.nb), 256, 0, cs>>>(a, aa));
+    if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_remap_adj<F>, dim3(FF / 256, a.nb), 256, 0, cs, a, aa));
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       if (store) {
         PTY_LAUNCH(p, kColAdj, cs,
-                   k_col_adj<F, true><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs>>>(S, a, aa));
+                   launch_pdl(k_col_adj<F, true>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs, S, a, aa));
       } else {
-        PTY_LAUNCH(p, kRowFwd, cs,
-                   k_row_fwd<F><<<dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs>>>(c.O, c.P, S, a));
+        if (rerun_rows)
+          PTY_LAUNCH(p, kRowFwd, cs,
+                     launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
         PTY_LAUNCH(p, kColAdj, cs,
-                   k_col_adj<F, false><<<dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs>>>(S, a, aa));
+                   launch_pdl(k_col_adj<F, false>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs, S, a, aa));
       }
       // the probe and object gradients accumulate in batch order across the two streams
       if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_radj[(k - 1) % nsets], 0) != cudaSuccess)
         return PTYCHO_ECUDA;
-      PTY_LAUNCH(p, kRowAdj, cs,
-                 k_row_adj<F><<<dim3(F / RowAdjCfg<F>::RPB, a.chunk_len), RowAdjCfg<F>::threads, RowAdjCfg<F>::smem,
-                                cs>>>(c.O, c.P, S, c.gP, a));
+      if (obj_atomic)
+        PTY_LAUNCH(p, kRowAdj, cs,
+                   launch_pdl(k_row_adj<F, true>, dim3(F / RowAdjCfg<F>::RPB, a.chunk_len), RowAdjCfg<F>::threads, RowAdjCfg<F>::smem, cs, c.O, c.P, S, c.gP, c.gO, a));
+      else
+        PTY_LAUNCH(p, kRowAdj, cs,
+                   launch_pdl(k_row_adj<F, false>, dim3(F / RowAdjCfg<F>::RPB, a.chunk_len), RowAdjCfg<F>::threads, RowAdjCfg<F>::smem, cs, c.O, c.P, S, c.gP, c.gO, a));
       if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+      if (obj_atomic) continue;
       if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_og[(k - 1) % nsets], 0) != cudaSuccess)
         return PTYCHO_ECUDA;
-      PTY_LAUNCH(p, kObjGrad, cs, k_obj_grad<F><<<dim3(max_tiles, p.L), 256, 0, cs>>>(S, c.gO, a));
+      PTY_LAUNCH(p, kObjGrad, cs, launch_pdl(k_obj_grad<F>, dim3(max_tiles, p.L), 256, 0, cs, S, c.gO, a));
       if (nsets > 1 && cudaEventRecord(p.ev_og[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
     }
   }
@@ -180,7 +206,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     double* out = c.loss;
     if (out) {
       PTY_LAUNCH(p, kLossReduce, st,
-                 k_loss_reduce<<<1, 256, 0, st>>>(p.d_loss_part, (long long)c.nbatch * (FF / kLossThreads), out));
+                 launch_pdl(k_loss_reduce, 1, 256, 0, st, p.d_loss_part, (long long)c.nbatch * (FF / kLossThreads), out));
     }
   }
   return PTYCHO_OK;

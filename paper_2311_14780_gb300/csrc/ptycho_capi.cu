@@ -12,6 +12,7 @@ namespace ptycho {
 
 // Fixed-order FP64 sum of the per-block loss partials (one block).
 __global__ void __launch_bounds__(256) k_loss_reduce(const double* __restrict__ part, long long n, double* out) {
+  pdl_wait();
   __shared__ double red[256];
   double s = 0.0;
   for (long long i = threadIdx.x; i < n; i += 256) s += part[i];
@@ -268,6 +269,10 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   p->L = g->L; p->M = g->M; p->F = F; p->J = g->J;
   p->remap = g->remap ? 1 : 0;
   p->loss_kind = g->loss;
+  p->flags = g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_OBJ_GRAD_ATOMIC);
+  // measured: recomputing the column DFT beats keeping Psi from F = 256 up
+  if (!(g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_KEEP_PSI)) && g->F >= 256)
+    p->flags |= PTYCHO_FLAG_RECOMPUTE_COLUMNS;
   p->eps = g->eps;
   long long off = 0;
   for (int l = 0; l < g->L; ++l) {
@@ -314,6 +319,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   }
   const long long target = 4ll * p->sms;
   long long G = (target + (long long)colblocks * p->B - 1) / ((long long)colblocks * p->B);
+  if (g->col_groups > 0) G = g->col_groups;
   G = std::max<long long>(1, std::min<long long>(G, p->C));
   p->MG = (int)((p->C + G - 1) / G);
   p->G = (p->C + p->MG - 1) / p->MG;

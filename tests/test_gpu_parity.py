@@ -316,3 +316,15 @@ def test_config4_full_size_sampled(dev):
     positions): sampled frames and the gradient of one position against the oracle."""
     w = syn.config4()
     assert_ok(_sampled_full_size(dev, w, n_frames=2, n_grad=1, seed=4))
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3, 4])
+@pytest.mark.parametrize("F", [64, 256])
+def test_pipeline_variants(dev, flags, F):
+    """Recompute-the-columns, atomic object-gradient and keep-Psi variants meet the same bars."""
+    w = syn.tiny_workload(F=F, L=2, M=3, n_side=4, step=F // 8, seed=60 + flags, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(F), mask_kind="frame", seed=flags)
+    plan = case.plan(flags=flags, scratch_bytes=5 * 6 * F * F * 8)    # several batches in flight
+    assert_ok(check_all(case, plan))
+    plan.close()
