@@ -57,10 +57,16 @@ extern "C" {
  * KEEP_PSI: keep Psi between the passes (the default for F < 256).
  * OBJ_GRAD_ATOMIC: the row adjoint adds the object gradient with FP32 atomics instead of
  *   the tile-owned gather (faster; the summation order, and so the last bits of grad O,
- *   then vary between runs). */
+ *   then vary between runs).
+ * TMA / NO_TMA: the column passes stage each mode's column block in shared memory with
+ *   bulk tensor copies (TMA) / read S with ordinary loads.  Default: TMA for F >= 512,
+ *   where it measured faster; below that the larger shared-memory footprint costs more
+ *   occupancy than the copies save.  NO_TMA wins when both are given. */
 #define PTYCHO_FLAG_RECOMPUTE_COLUMNS 1
 #define PTYCHO_FLAG_OBJ_GRAD_ATOMIC 2
 #define PTYCHO_FLAG_KEEP_PSI 4
+#define PTYCHO_FLAG_NO_TMA 8
+#define PTYCHO_FLAG_TMA 16
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */
@@ -165,8 +171,11 @@ int64_t ptycho_plan_last_launches(const ptycho_plan_t* plan);
 
 /* Device-side status of the plan since the previous query, then cleared.  Bit 0
  * (PTYCHO_STATUS_BAD_INDEX): a batch_idx entry was outside [0, J); that position was
- * skipped.  Synchronises the device (call it outside the timed loop). */
+ * skipped.  Bit 1 (PTYCHO_STATUS_WAIT_TIMEOUT): a bulk shared-memory copy of a column pass
+ * did not complete within about a second; the block gave up and its outputs for that call
+ * are not valid.  Synchronises the device (call it outside the timed loop). */
 #define PTYCHO_STATUS_BAD_INDEX 1
+#define PTYCHO_STATUS_WAIT_TIMEOUT 2
 int ptycho_plan_status(ptycho_plan_t* plan, int32_t* flags);
 
 /* Plain (unfused) form of ptycho_step, the baseline the fused path is measured against:

@@ -19,6 +19,8 @@ LOSS_CODES = {"amplitude": 0, "poisson": 1}
 FLAG_RECOMPUTE_COLUMNS = 1
 FLAG_OBJ_GRAD_ATOMIC = 2
 FLAG_KEEP_PSI = 4
+FLAG_NO_TMA = 8
+FLAG_TMA = 16
 
 
 class PtychoError(RuntimeError):
@@ -138,7 +140,8 @@ class Plan:
                 for k in range(_native.NUM_KERNELS)}
 
     def status(self) -> int:
-        """Device status flags since the last query (synchronises; bit 0 = bad batch index)."""
+        """Device status flags since the last query (synchronises; bit 0 = bad batch index,
+        bit 1 = a column pass's bulk copy timed out)."""
         v = ctypes.c_int32(0)
         _check(_native.lib().ptycho_plan_status(self._h_plan, ctypes.byref(v)), "ptycho_plan_status")
         return int(v.value)

@@ -22,6 +22,7 @@
 //   k_adam      Adam on the real and imaginary parts of O and P
 #pragma once
 #include "fft_regs.cuh"
+#include "tma.cuh"
 
 namespace ptycho {
 
@@ -166,6 +167,89 @@ k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_
       acc[sl] = fmaf(v[sl].x, v[sl].x, fmaf(v[sl].y, v[sl].y, acc[sl]));
       if (STORE) base[(long long)idxO<F>(t, sl) * F] = cscale(v[sl], inv);
     }
+  }
+  float* dst = Ipart + ((long long)b * a.G + g) * F * F;
+  const int cc = (col + F / 2) & (F - 1);
+#pragma unroll
+  for (int sl = 0; sl < N2; ++sl) {
+    const int rc = (idxO<F>(t, sl) + F / 2) & (F - 1);
+    float val = acc[sl] * (inv * inv);
+    if (!first_chunk) val += dst[rc * F + cc];
+    dst[rc * F + cc] = val;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// TMA-staged column passes.  The W x F column block of one mode (W*F*8 bytes) arrives in
+// shared memory through cp.async.bulk.tensor (2D tensor map over S viewed as
+// [B*C*F rows][F columns] of 8-byte elements); the next mode's block is requested as soon as
+// every thread has read the current one into registers, so the copy overlaps the FFT.
+// ---------------------------------------------------------------------------------------
+template <int F> struct ColTma {
+  static constexpr int W = ColCfg<F>::W;
+  static constexpr int box_rows = F < 256 ? F : 256;
+  static constexpr int stage_bytes = F * W * (int)sizeof(float2);
+  static constexpr int smem_fwd = stage_bytes + ColCfg<F>::smem_xch + 16;
+  static constexpr int smem_adj = smem_fwd + F * W * (int)sizeof(float);
+};
+
+template <int F>
+__device__ __forceinline__ void col_tma_issue(float2* stage, const CUtensorMap* map, int col0, int row0, uint64_t* bar) {
+  fence_proxy_async_smem();                    // earlier generic reads of the stage come first
+  mbar_arrive_expect_tx(bar, ColTma<F>::stage_bytes);
+#pragma unroll
+  for (int h = 0; h < F / ColTma<F>::box_rows; ++h)
+    tma_load_2d(stage + h * ColTma<F>::box_rows * ColTma<F>::W, map, col0, row0 + h * ColTma<F>::box_rows, bar);
+}
+
+// grid (F/W, G, nb); same results as k_col_fwd
+template <int F, bool STORE>
+__global__ void __launch_bounds__(ColCfg<F>::threads)
+k_col_fwd_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, float* __restrict__ Ipart, KArgs a,
+              int first_chunk) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
+  extern __shared__ __align__(128) float2 smem[];
+  float2* stage = smem;
+  float2* xch = smem + F * W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + W * Xch<F>::region_cols);
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int col0 = blockIdx.x * W, col = col0 + c;
+  const int g = blockIdx.y, b = blockIdx.z;
+  const int m0 = g * a.MG, m1 = min(a.chunk_len, m0 + a.MG);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && m0 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + m0) * F, bar);
+  float acc[N2];
+#pragma unroll
+  for (int i = 0; i < N2; ++i) acc[i] = 0.f;
+  const float inv = 1.0f / (float)F;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int cm = m0; cm < m1; ++cm) {
+    ok = __syncthreads_and(mbar_wait_bounded(bar, phase, a.status));
+    if (!ok) break;
+    phase ^= 1;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = stage[(t + N1 * n2) * W + c];
+    __syncthreads();                           // the stage is free for the next mode
+    if (threadIdx.x == 0 && cm + 1 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + cm + 1) * F, bar);
+    fft_fwd_I2O<F>(v, t, xch + c * Xch<F>::region_cols, a.tw, BlockSync{});
+    float2* base = S + ((long long)b * a.C + cm) * F * F + col;
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) {
+      acc[sl] = fmaf(v[sl].x, v[sl].x, fmaf(v[sl].y, v[sl].y, acc[sl]));
+      if (STORE) base[(long long)idxO<F>(t, sl) * F] = cscale(v[sl], inv);
+    }
+  }
+  if (!ok) {                                   // give a lost copy a bounded chance to land, then stop
+    if (threadIdx.x == 0) mbar_wait_bounded(bar, phase, a.status);
+    return;
   }
   float* dst = Ipart + ((long long)b * a.G + g) * F * F;
   const int cc = (col + F / 2) & (F - 1);
@@ -359,6 +443,68 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) base[(long long)(t + N1 * n2) * F] = v[n2];
   }
+}
+
+// grid (F/W, G, nb); same results as k_col_adj
+template <int F, bool STORE>
+__global__ void __launch_bounds__(ColCfg<F>::threads)
+k_col_adj_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
+  extern __shared__ __align__(128) float2 smem[];
+  float2* stage = smem;
+  float2* xch = smem + F * W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + W * Xch<F>::region_cols);
+  float* gt = reinterpret_cast<float*>(bar + 2);                    // [F][W]
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int col0 = blockIdx.x * W, col = col0 + c;
+  const int g = blockIdx.y, b = blockIdx.z;
+  const int m0 = g * a.MG, m1 = min(a.chunk_len, m0 + a.MG);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && m0 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + m0) * F, bar);
+  const float* Gb = (aa.remap ? aa.Gt : aa.D) + (long long)b * F * F;
+  const float scale = 2.0f / (float)F;
+  for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
+    const int k = e / W, ce = e % W;
+    const int u = ((k + F / 2) & (F - 1)) * F + ((col0 + ce + F / 2) & (F - 1));
+    gt[k * W + ce] = Gb[u] * scale;
+  }
+  __syncthreads();
+  const float inv = 1.0f / (float)F;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int cm = m0; cm < m1; ++cm) {
+    ok = __syncthreads_and(mbar_wait_bounded(bar, phase, a.status));
+    if (!ok) break;
+    phase ^= 1;
+    float2 v[N2];
+    if (STORE) {
+#pragma unroll
+      for (int sl = 0; sl < N2; ++sl) v[sl] = stage[idxO<F>(t, sl) * W + c];
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = stage[(t + N1 * n2) * W + c];
+    }
+    __syncthreads();                           // the stage is free for the next mode
+    if (threadIdx.x == 0 && cm + 1 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + cm + 1) * F, bar);
+    if (!STORE) {
+      fft_fwd_I2O<F>(v, t, xch + c * Xch<F>::region_cols, a.tw, BlockSync{});
+#pragma unroll
+      for (int sl = 0; sl < N2; ++sl) v[sl] = cscale(v[sl], inv);
+    }
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) v[sl] = cscale(v[sl], gt[idxO<F>(t, sl) * W + c]);
+    fft_inv_O2I<F>(v, t, xch + c * Xch<F>::region_cols, a.tw, BlockSync{});
+    float2* base = S + ((long long)b * a.C + cm) * F * F + col;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) base[(long long)(t + N1 * n2) * F] = v[n2];
+  }
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, phase, a.status);
 }
 
 // ---------------------------------------------------------------------------------------

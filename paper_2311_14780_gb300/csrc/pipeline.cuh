@@ -45,6 +45,10 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_fwd);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_fwd);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
   if (e != cudaSuccess) return PTYCHO_ECUDA;
   done = 1;
   return PTYCHO_OK;
@@ -155,14 +159,19 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       PTY_LAUNCH(p, kRowFwd, cs,
                  launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
-      if (store)
-        PTY_LAUNCH(p, kColFwd, cs,
-                   launch_pdl(k_col_fwd<F, true>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs, 
-                       S, Ip, a, ch == 0));
+      const dim3 col_grid(F / ColCfg<F>::W, p.G, a.nb);
+      if (p.has_tma && store)
+        PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
+                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
+      else if (p.has_tma)
+        PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, false>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
+                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
+      else if (store)
+        PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, true>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
+                                              (int)(ch == 0)));
       else
-        PTY_LAUNCH(p, kColFwd, cs,
-                   launch_pdl(k_col_fwd<F, false>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, ColCfg<F>::smem_xch, cs, 
-                       S, Ip, a, ch == 0));
+        PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, false>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
+                                              (int)(ch == 0)));
     }
     PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(FF / kLossThreads, a.nb), kLossThreads, 0, cs, a, la));
     if (!grad) continue;
@@ -170,17 +179,21 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
-      if (store) {
-        PTY_LAUNCH(p, kColAdj, cs,
-                   launch_pdl(k_col_adj<F, true>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs, S, a, aa));
-      } else {
-        if (rerun_rows)
-          PTY_LAUNCH(p, kRowFwd, cs,
-                     launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
-        PTY_LAUNCH(p, kColAdj, cs,
-                   launch_pdl(k_col_adj<F, false>, dim3(F / ColCfg<F>::W, p.G, a.nb), col_blk, col_adj_smem, cs, S, a, aa));
-      }
-      // the probe and object gradients accumulate in batch order across the two streams
+      const dim3 col_grid(F / ColCfg<F>::W, p.G, a.nb);
+      if (!store && rerun_rows)
+        PTY_LAUNCH(p, kRowFwd, cs,
+                   launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
+      if (p.has_tma && store)
+        PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_adj, cs,
+                                              p.tmap_S[set], S, a, aa));
+      else if (p.has_tma)
+        PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_tma<F, false>, col_grid, col_blk, ColTma<F>::smem_adj, cs,
+                                              p.tmap_S[set], S, a, aa));
+      else if (store)
+        PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj<F, true>, col_grid, col_blk, col_adj_smem, cs, S, a, aa));
+      else
+        PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj<F, false>, col_grid, col_blk, col_adj_smem, cs, S, a, aa));
+      // the probe and object gradients accumulate in batch order across the streams
       if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_radj[(k - 1) % nsets], 0) != cudaSuccess)
         return PTYCHO_ECUDA;
       if (obj_atomic)

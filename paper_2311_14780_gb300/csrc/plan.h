@@ -1,6 +1,7 @@
 // Host-side plan: geometry, validated positions, remap tables, batching decisions and the
 // device workspace.  Shared by the C-ABI front end and the per-frame-size pipelines.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -53,6 +54,11 @@ struct ptycho_plan {
   float2* d_gO = nullptr;
   float2* d_gP = nullptr;
   int* d_status = nullptr;                     // device status word, see ptycho_plan_status
+
+  // TMA tensor maps of each scratch set, viewed as [B*C*F rows][F columns] of 8-byte elements
+  // with a W x min(F, 256) box (column passes); has_tma = 0 falls back to plain loads
+  int has_tma = 0;
+  alignas(64) CUtensorMap tmap_S[4];
   long long bytes = 0;
   long long last_launches = 0;
 

@@ -6,6 +6,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "plan.h"
 
 namespace ptycho {
@@ -194,6 +196,36 @@ void build_remap(int F, double z, double p, double alpha, std::vector<int32_t>& 
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static int tried = 0;
+  if (!tried) {
+    tried = 1;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D map over a scratch set: rows of F complex64 (8-byte elements), box W x min(F, 256).
+bool make_column_map(CUtensorMap* map, void* base, int F, long long rows, int W) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)F, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)F * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)(F < 256 ? F : 256)};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int check_device(const ptycho_plan* p) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return PTYCHO_ECUDA;
@@ -354,6 +386,21 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   rc = rc ? rc : dalloc(p, &p->d_status, 1);
   if (!rc && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = PTYCHO_ECUDA;
   if (rc) { free_plan(p); return rc; }
+  {
+    int W = 0;
+    switch (F) {
+      case 64: W = ptycho::ColCfg<64>::W; break;
+      case 128: W = ptycho::ColCfg<128>::W; break;
+      case 256: W = ptycho::ColCfg<256>::W; break;
+      default: W = ptycho::ColCfg<512>::W; break;
+    }
+    const long long rows = (long long)p->B * p->C * F;
+    // measured: the staged column passes pay off from F = 512 up
+    p->has_tma = (g->flags & PTYCHO_FLAG_NO_TMA) ? 0 : ((g->flags & PTYCHO_FLAG_TMA) || F >= 512) ? 1 : 0;
+    for (int i = 0; i < p->nsets; ++i)
+      if (p->has_tma && !make_column_map(&p->tmap_S[i], p->d_S + (long long)i * p->B * p->C * FF, F, rows, W))
+        p->has_tma = 0;
+  }
 
   std::vector<int32_t> ident(g->J);
   for (int j = 0; j < g->J; ++j) ident[j] = j;

@@ -101,11 +101,12 @@ def check_all(case, plan, frames=None):
     Lr, gOr, gPr = case.oracle_grad(frames)
     gOr = np.concatenate([g.reshape(-1) for g in gOr])
     out = dict(I=e_I, L=abs(Lg - Lr) / abs(Lr), La=abs(float(La.item()) - Lr) / abs(Lr),
-               gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr))
+               gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr), status=plan.status())
     return out
 
 
 def assert_ok(err):
+    assert err.get("status", 0) == 0, err          # no bad index, no timed-out bulk copy
     assert err["I"] < TOL_I, err
     assert err["L"] < TOL_L and err["La"] < TOL_L, err
     assert err["gO"] < TOL_G and err["gP"] < TOL_G, err
@@ -271,6 +272,26 @@ def test_deterministic_repeat(dev):
     plan.close()
 
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_overlapped_batches_match_one_stream(dev, flags):
+    """Batches in flight on four streams add into the gradients in batch order: bit-identical
+    to the same batches on one stream (a missing cross-stream ordering shows up here)."""
+    w = syn.tiny_workload(F=64, L=2, M=3, n_side=6, step=8, seed=7, remap=True, loss="poisson", with_sigma=True)
+    case = Case(w, dev, z=strong_z(64), seed=7)
+    scratch = 2 * 6 * 64 * 64 * 8                                 # two positions per batch: 18 batches
+    res = []
+    for overlap in (1, 4):
+        plan = case.plan(scratch_bytes=scratch, overlap=overlap, flags=flags)
+        res.append([plan.adjoint(case.O, case.P, case.Im, case.sig_t) for _ in range(3)])
+        plan.close()
+    ref = res[0][0]
+    for run in res[0][1:] + res[1]:
+        assert torch.equal(run[0], ref[0])
+        assert torch.equal(run[2], ref[2])                      # grad P: register sums in batch order
+        if flags == 0:                                          # grad O: tile-owned, in batch order
+            assert torch.equal(run[1], ref[1])
+
+
 def _sampled_full_size(dev, w, n_frames, n_grad, seed):
     """Full-size plan; predicted frames of a sample and the gradient of a smaller subset
     checked against the oracle, at a near-truth evaluation point."""
@@ -318,10 +339,11 @@ def test_config4_full_size_sampled(dev):
     assert_ok(_sampled_full_size(dev, w, n_frames=2, n_grad=1, seed=4))
 
 
-@pytest.mark.parametrize("flags", [1, 2, 3, 4])
+@pytest.mark.parametrize("flags", [1, 2, 3, 4, 16, 17, 20])
 @pytest.mark.parametrize("F", [64, 256])
 def test_pipeline_variants(dev, flags, F):
-    """Recompute-the-columns, atomic object-gradient and keep-Psi variants meet the same bars."""
+    """Recompute-the-columns, atomic object-gradient, keep-Psi and TMA-staged column variants
+    meet the same bars."""
     w = syn.tiny_workload(F=F, L=2, M=3, n_side=4, step=F // 8, seed=60 + flags, remap=True, loss="poisson",
                           with_sigma=True, with_bg=True)
     case = Case(w, dev, z=strong_z(F), mask_kind="frame", seed=flags)
