@@ -34,7 +34,9 @@ Parity pins: see ``tests/test_oracle_pins.py`` (brute-force DFT, Parseval, unita
 mode-mixing and global-phase invariance, closed-form diffraction of plane waves,
 zero loss and zero gradient at noiseless truth, central finite differences, remap
 dot-product / identity / constant tests, the Adam first-step closed form and the
-paper's geometry numbers).  The tilted-plane remap formula itself is a reading of the
+paper's geometry numbers; for the sigma and background gradients: finite differences,
+the intensity-level form of the sigma gradient that Parseval's theorem gives, and the
+identity between the sigma gradient and the probe gradient along P -> cP).  The tilted-plane remap formula itself is a reading of the
 cited geometry and is only partially pinned (identity limit, constants, adjointness,
 the paper's NA and pixel-ratio figures).
 """
@@ -291,6 +293,40 @@ def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=N
     return total, gO, gP
 
 
+def gradient_sigma_bg(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None):
+    """Loss and its gradient with respect to the power coefficients sigma_j and the
+    background N (two of the model variables the paper lists as optimisable, Section
+    "Universal Ptychography Algorithm", the paragraph after Eq. 2).
+
+    sigma_j is a real factor of every probe mode of frame j (f1), so by the chain rule
+    through the exit wave dL/dsigma_j = sum_{l,m} sum_r Re(conj(P_lm p_jl) chi_jlm), with
+    chi the exit-wave gradient of ``gradient``.  N is added to the incoherent sum on the
+    model grid before the remap (Eq. 1), so dL/dN = sum_j G_j with G_j = R^T(mask dL/dI_cam).
+    Returns (loss, g_sigma [J] (0 for frames not requested), g_bg [F, F]).
+    """
+    L, M, F = P.shape[0], P.shape[1], P.shape[2]
+    J = pos.shape[1]
+    frames = range(J) if frames is None else frames
+    g_sigma = np.zeros(J)
+    g_bg = np.zeros((F, F))
+    total = 0.0
+    for j in frames:
+        patches, Psi = frame_fields(O, P, pos, j, sigma)
+        I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
+        Ic = f5_measure(I_sum, bg, taps)
+        mk = frame_mask(mask, j, F, taps)
+        total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
+        with np.errstate(divide="ignore", invalid="ignore"):
+            D = np.where(mk, loss_derivative(Ic, Imeas[j], kind, eps), 0.0)
+        G = D if taps is None else remap_adjoint(D, taps)
+        g_bg += G
+        for l in range(L):
+            for m in range(M):
+                chi = f4_adjoint(2.0 * G * Psi[l, m])
+                g_sigma[j] += float(np.real(np.conj(P[l, m] * patches[l]) * chi).sum())
+    return total, g_sigma, g_bg
+
+
 # ----------------------------------------------------------------------------
 # Adam (Kingma & Ba), real and imaginary parts as separate real parameters
 # ----------------------------------------------------------------------------
@@ -320,6 +356,36 @@ def adam_update(theta: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, 
     vhat = v / (1.0 - b2 ** t)
     upd = lr * mhat / (np.sqrt(vhat) + eps)
     return theta - (upd[..., 0] + 1j * upd[..., 1])
+
+
+def adam_update_real(theta: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int,
+                     lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam step on a real array; m and v (same shape) are updated in place."""
+    m *= b1
+    m += (1.0 - b1) * g
+    v *= b2
+    v += (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps)
+
+
+def step_sigma_bg(O, P, sigma, bg, pos, Imeas, kind, eps, state: AdamState, m_sigma, v_sigma, m_bg, v_bg,
+                  lr_O: float, lr_P: float, lr_sigma: float, lr_bg: float, b1=0.9, b2=0.999, adam_eps=1e-8,
+                  mask=None, taps=None, frames=None):
+    """One step that also optimises sigma ([J]) and the background ([F, F]) with Adam; every
+    component of sigma takes the update (its gradient is 0 for frames outside ``frames``).
+    Returns (loss, O, P, sigma, bg)."""
+    total, gO, gP = gradient(O, P, pos, Imeas, kind, eps, sigma, bg, mask, taps, frames)
+    _, g_sigma, g_bg = gradient_sigma_bg(O, P, pos, Imeas, kind, eps, sigma, bg, mask, taps, frames)
+    state.t += 1
+    O_new = [adam_update(O[l], gO[l], state.mO[l], state.vO[l], state.t, lr_O, b1, b2, adam_eps)
+             for l in range(len(O))]
+    P_new = adam_update(P, gP, state.mP, state.vP, state.t, lr_P, b1, b2, adam_eps)
+    s_new = adam_update_real(np.asarray(sigma, np.float64), g_sigma, m_sigma, v_sigma, state.t, lr_sigma, b1, b2,
+                             adam_eps)
+    bg_new = adam_update_real(np.asarray(bg, np.float64), g_bg, m_bg, v_bg, state.t, lr_bg, b1, b2, adam_eps)
+    return total, O_new, P_new, s_new, bg_new
 
 
 def step(O, P, pos, Imeas, kind, eps, state: AdamState, lr_O: float, lr_P: float,

@@ -294,6 +294,95 @@ def test_masked_pixels_do_not_enter_the_loss():
 
 
 # ----------------------------------------------------------------------------
+# power coefficients sigma_j and background N
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", orc.LOSS_KINDS)
+@pytest.mark.parametrize("remap,with_mask", [(False, False), (True, True)])
+def test_sigma_bg_gradient_matches_central_finite_differences(kind, remap, with_mask):
+    w, taps, Ih, mask = _fd_case(kind, remap, with_mask)
+    eps = 1e-3
+    _, g_s, g_bg = orc.gradient_sigma_bg(w.O0, w.P0, w.pos, Ih, kind, eps, w.sigma, w.bg, mask, taps)
+
+    def L(sig, bg):
+        return orc.loss(w.O0, w.P0, w.pos, Ih, kind, eps, sig, bg, mask, taps)
+
+    h = 1e-5
+    L0 = abs(L(w.sigma, w.bg))
+    noise = 50 * 2.2e-16 * L0 / h
+    rng = np.random.default_rng(12)
+    for j in rng.choice(w.J, size=3, replace=False):
+        sp, sm = w.sigma.astype(np.float64).copy(), w.sigma.astype(np.float64).copy()
+        sp[j] += h
+        sm[j] -= h
+        fd = (L(sp, w.bg) - L(sm, w.bg)) / (2 * h)
+        assert abs(fd - g_s[j]) <= 1e-6 * abs(g_s[j]) + noise, (fd, g_s[j])
+    for _ in range(4):
+        r, c = rng.integers(w.F // 4, 3 * w.F // 4, size=2)
+        bp, bm = w.bg.astype(np.float64).copy(), w.bg.astype(np.float64).copy()
+        bp[r, c] += h
+        bm[r, c] -= h
+        fd = (L(w.sigma, bp) - L(w.sigma, bm)) / (2 * h)
+        assert abs(fd - g_bg[r, c]) <= 1e-6 * abs(g_bg[r, c]) + noise, (fd, g_bg[r, c])
+
+
+def test_sigma_gradient_equals_its_intensity_form():
+    """Parseval: sum_r conj(psi) chi = 2 sum_k G_k |Psi_k|^2, so
+    sigma_j dL/dsigma_j = 2 sum_u G_ju (I_ju - N_u) on the model grid."""
+    w, taps, Ih, mask = _fd_case("poisson", True, True)
+    eps = 1e-3
+    _, g_s, _ = orc.gradient_sigma_bg(w.O0, w.P0, w.pos, Ih, "poisson", eps, w.sigma, w.bg, mask, taps)
+    for j in range(w.J):
+        _, Psi = orc.frame_fields(w.O0, w.P0, w.pos, j, w.sigma)
+        I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
+        Ic = orc.f5_measure(I_sum, w.bg, taps)
+        mk = orc.frame_mask(mask, j, w.F, taps)
+        D = np.where(mk, orc.loss_derivative(Ic, Ih[j], "poisson", eps), 0.0)
+        G = orc.remap_adjoint(D, taps)
+        exp = 2.0 * float((G * I_sum).sum()) / float(w.sigma[j])
+        assert abs(g_s[j] - exp) < 1e-9 * max(abs(exp), 1e-30), (j, g_s[j], exp)
+
+
+def test_sigma_gradient_matches_probe_gradient_along_scaling():
+    """sigma_j multiplies P, so scaling every sigma by c equals scaling P by c:
+    sum_j sigma_j dL/dsigma_j = Re <P, grad P> (sum over all modes)."""
+    w, taps, Ih, mask = _fd_case("amplitude", True, True)
+    args = (w.pos, Ih, "amplitude", 1e-3, w.sigma, w.bg, mask, taps)
+    _, _, gP = orc.gradient(w.O0, w.P0, *args)
+    _, g_s, _ = orc.gradient_sigma_bg(w.O0, w.P0, *args)
+    lhs = float((w.sigma * g_s).sum())
+    rhs = float(np.real(np.vdot(w.P0, gP)))
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs)
+
+
+@pytest.mark.parametrize("remap", [False, True])
+def test_sigma_bg_gradients_vanish_at_noiseless_truth(remap):
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=15, remap=remap, with_bg=True, with_sigma=True)
+    taps = orc.remap_taps(w.F, 2e-3, 15e-6, math.radians(70)) if remap else None
+    Ih = orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps)
+    _, g_s, g_bg = orc.gradient_sigma_bg(w.O_true, w.P_true, w.pos, Ih, "poisson", 0.0, w.sigma, w.bg, None, taps)
+    assert np.abs(g_s).max() < 1e-12 and np.abs(g_bg).max() < 1e-12
+
+
+def test_sigma_gradient_is_zero_for_frames_not_requested():
+    w, taps, Ih, mask = _fd_case("poisson", False, False)
+    _, g_s, g_bg = orc.gradient_sigma_bg(w.O0, w.P0, w.pos, Ih, "poisson", 1e-3, w.sigma, w.bg, None, None,
+                                         frames=[1, 3])
+    _, g1, b1 = orc.gradient_sigma_bg(w.O0, w.P0, w.pos, Ih, "poisson", 1e-3, w.sigma, w.bg, None, None, frames=[1])
+    _, g3, b3 = orc.gradient_sigma_bg(w.O0, w.P0, w.pos, Ih, "poisson", 1e-3, w.sigma, w.bg, None, None, frames=[3])
+    assert np.count_nonzero(g_s) == 2 and g_s[1] == g1[1] and g_s[3] == g3[3]
+    assert np.abs(g_bg - (b1 + b3)).max() < 1e-12 * np.abs(g_bg).max()
+
+
+def test_adam_real_first_step_closed_form():
+    rng = np.random.default_rng(16)
+    th, g = rng.normal(size=9), rng.normal(size=9)
+    m, v = np.zeros(9), np.zeros(9)
+    out = orc.adam_update_real(th, g, m, v, 1, 0.05)
+    assert np.abs(out - (th - 0.05 * g / (np.abs(g) + 1e-8))).max() < 1e-15
+
+
+# ----------------------------------------------------------------------------
 # tilted-plane remap
 # ----------------------------------------------------------------------------
 
