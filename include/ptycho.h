@@ -113,6 +113,12 @@ typedef struct {
                                ptycho_step increments it on the device and the bias
                                correction reads it there, so a captured CUDA graph of
                                ptycho_step can be replayed; t is then left unchanged  */
+  /* Optional: the power coefficients sigma and the background N are optimised too (the
+   * paper lists both among the variables it reconstructs, and initialises them to 1). */
+  float lr_sigma;           /* > 0: ptycho_step updates sigma [J] in place              */
+  float lr_bg;              /* > 0: ptycho_step updates bg [F][F] in place              */
+  float* m_sigma; float* v_sigma;   /* [J], required when lr_sigma > 0                  */
+  float* m_bg; float* v_bg;         /* [F*F], required when lr_bg > 0                   */
 } ptycho_adam_t;
 
 /* Validates the geometry and every scan position (PTYCHO_ERANGE names an out-of-object
@@ -159,11 +165,31 @@ int ptycho_adjoint(ptycho_plan_t* plan, const float* O, const float* P, const fl
                    const int32_t* batch_idx, int nbatch, float* gO, float* gP, double* loss_dev,
                    void* stream);
 
+/* ptycho_adjoint that also returns the gradients with respect to the power coefficients
+ * and the background (the paper's sigma_k and N(rho), Eq. 1), each optional (NULL = not
+ * computed):
+ *   g_sigma [J] OVERWRITTEN: dL/dsigma_j for every position in the call, 0 for the others.
+ *           Computed from the intensities: sigma_j enters every exit wave of frame j as a
+ *           real factor and the DFT is unitary, so dL/dsigma_j = (2 / sigma_j) times the
+ *           sum over the camera grid of (mask dL/dI) * (R sum_lm |Psi_jlm|^2); 0 where
+ *           sigma_j = 0 (the derivative vanishes there).  sigma NULL means all ones.
+ *   g_bg    [F][F] OVERWRITTEN: dL/dN on the model grid (N is added before the remap),
+ *           the sum over the call's positions of R^T(mask dL/dI); deterministic for a
+ *           given plan (per-stream partial sums added in a fixed order).
+ * Other arguments as for ptycho_adjoint. */
+int ptycho_adjoint_ex(ptycho_plan_t* plan, const float* O, const float* P, const float* sigma,
+                      const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
+                      const int32_t* batch_idx, int nbatch, float* gO, float* gP, float* g_sigma,
+                      float* g_bg, double* loss_dev, void* stream);
+
 /* One optimisation step on a batch of positions ("per batch" updates, Fig. 2 caption):
  * ptycho_adjoint into plan-owned gradient buffers, then Adam on O (lr_O) and P (lr_P) in
- * place.  state->t is incremented on the host before the update. */
-int ptycho_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, const float* sigma,
-                const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
+ * place, and on sigma (lr_sigma > 0) and bg (lr_bg > 0) in place when the state asks for
+ * it (sigma / bg must then be non-NULL; every component of sigma takes the Adam update,
+ * with gradient 0 for positions outside the batch).  state->t is incremented on the host
+ * before the update. */
+int ptycho_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, float* sigma,
+                float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
                 const int32_t* batch_idx, int nbatch, double* loss_dev, void* stream);
 
 /* Number of kernel launches issued by the most recent compute call on this plan. */
@@ -183,7 +209,8 @@ int ptycho_plan_status(ptycho_plan_t* plan, int32_t* flags);
  * gradient scatter) is a separate kernel, exit waves go through a device buffer that the
  * call allocates (stream-ordered), and gradients are scattered with FP32 atomics (so their
  * summation order, and the last bits of the result, can vary between runs).  Arguments as
- * for ptycho_step with all positions. */
+ * for ptycho_step with all positions; it updates O and P only (PTYCHO_EUNSUPPORTED when the
+ * state asks for sigma or background updates). */
 int ptycho_plain_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, const float* sigma,
                       const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
                       double* loss_dev, void* stream);

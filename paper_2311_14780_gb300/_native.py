@@ -32,6 +32,9 @@ class Adam(ctypes.Structure):
         ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("t", ctypes.c_int32),
         ("mO", ctypes.c_void_p), ("vO", ctypes.c_void_p), ("mP", ctypes.c_void_p), ("vP", ctypes.c_void_p),
         ("t_dev", ctypes.c_void_p),
+        ("lr_sigma", ctypes.c_float), ("lr_bg", ctypes.c_float),
+        ("m_sigma", ctypes.c_void_p), ("v_sigma", ctypes.c_void_p), ("m_bg", ctypes.c_void_p),
+        ("v_bg", ctypes.c_void_p),
     ]
 
 
@@ -57,6 +60,7 @@ SIGNATURES = [
     ("ptycho_forward", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ptycho_loss", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     ("ptycho_adjoint", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP]),
+    ("ptycho_adjoint_ex", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ptycho_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     ("ptycho_plan_status", _I, [_VP, c_int32_p]),
     ("ptycho_plan_profile", _I, [_VP, _I]),

@@ -237,9 +237,29 @@ class Plan:
         _check(rc, "ptycho_adjoint")
         return loss_out, gO, gP
 
+    def adjoint_ex(self, O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, stream=None):
+        """ptycho_adjoint_ex: (loss, grad O, grad P, grad sigma [J], grad bg [F, F])."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        m, mpf = self._mask(mask)
+        bt, nb = self._batch(batch)
+        gO = torch.empty(self.numel_O, dtype=torch.complex64, device=self.device)
+        gP = torch.empty(P.shape, dtype=torch.complex64, device=self.device)
+        gs = torch.empty(self.J, dtype=torch.float32, device=self.device)
+        gb = torch.empty(self.F, self.F, dtype=torch.float32, device=self.device)
+        loss_out = torch.zeros(1, dtype=torch.float64, device=self.device)
+        rc = _native.lib().ptycho_adjoint_ex(self._h_plan, _ptr(Or), _ptr(Pr), _ptr(self._f32(sigma, self.J, "sigma")),
+                                             _ptr(self._f32(bg, FF, "bg")),
+                                             _ptr(self._f32(Imeas, self.J * FF, "Imeas")), _ptr(m), mpf, _ptr(bt), nb,
+                                             _ptr(gO), _ptr(gP), _ptr(gs), _ptr(gb), _ptr(loss_out),
+                                             _stream_handle(stream))
+        _check(rc, "ptycho_adjoint_ex")
+        return loss_out, gO, gP, gs, gb
+
     def step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, loss_out=None,
              stream=None):
-        """ptycho_step: adjoint + fused Adam on O and P in place; returns the FP64 loss tensor."""
+        """ptycho_step: adjoint + fused Adam on O and P in place (and on sigma / bg when the state
+        has lr_sigma / lr_bg > 0); returns the FP64 loss tensor."""
         FF = self.F * self.F
         Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
         m, mpf = self._mask(mask)
@@ -254,7 +274,6 @@ class Plan:
         _check(rc, "ptycho_step")
         state.t = int(st.t)
         return loss_out
-
 
     def plain_step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, loss_out=None,
                    stream=None):
@@ -278,8 +297,15 @@ class AdamState:
     """Adam moments for O and P (device tensors, 2 floats per complex element)."""
 
     def __init__(self, plan: Plan, lr_O: float, lr_P: float, beta1: float = 0.9, beta2: float = 0.999,
-                 eps: float = 1e-8, device_counter: bool = False):
+                 eps: float = 1e-8, device_counter: bool = False, lr_sigma: float = 0.0, lr_bg: float = 0.0):
         dev = plan.device
+        # optional: sigma [J] and the background [F, F] are optimised too (updated in place by
+        # Plan.step, which then needs them as float32 device tensors)
+        self.lr_sigma, self.lr_bg = lr_sigma, lr_bg
+        self.m_sigma = torch.zeros(plan.J, dtype=torch.float32, device=dev) if lr_sigma > 0 else None
+        self.v_sigma = torch.zeros_like(self.m_sigma) if lr_sigma > 0 else None
+        self.m_bg = torch.zeros(plan.F * plan.F, dtype=torch.float32, device=dev) if lr_bg > 0 else None
+        self.v_bg = torch.zeros_like(self.m_bg) if lr_bg > 0 else None
         # with a device step counter a captured CUDA graph of Plan.step can be replayed
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=dev) if device_counter else None
         self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps = lr_O, lr_P, beta1, beta2, eps
@@ -295,6 +321,10 @@ class AdamState:
         s.mO, s.vO = self.mO.data_ptr(), self.vO.data_ptr()
         s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
         s.t_dev = None if self.t_dev is None else self.t_dev.data_ptr()
+        s.lr_sigma, s.lr_bg = self.lr_sigma, self.lr_bg
+        for name in ("m_sigma", "v_sigma", "m_bg", "v_bg"):
+            t = getattr(self, name)
+            setattr(s, name, None if t is None else t.data_ptr())
         return s
 
 

@@ -16,20 +16,35 @@ from .api import Plan
 class PtychoLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, O, P, plan: Plan, Imeas, sigma=None, bg=None, mask=None, batch=None):
-        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
-            loss, gO, gP = plan.adjoint(O.detach(), P.detach(), Imeas, sigma, bg, mask, batch)
+        need = ctx.needs_input_grad
+        sb = (len(need) > 4 and need[4]) or (len(need) > 5 and need[5])
+        s_d = None if sigma is None else sigma.detach()
+        b_d = None if bg is None else bg.detach()
+        if sb:
+            loss, gO, gP, gs, gb = plan.adjoint_ex(O.detach(), P.detach(), Imeas, s_d, b_d, mask, batch)
+            ctx.save_for_backward(gO, gP, gs.reshape(sigma.shape) if sigma is not None else gs,
+                                  gb.reshape(bg.shape) if bg is not None else gb)
+        elif need[0] or need[1]:
+            loss, gO, gP = plan.adjoint(O.detach(), P.detach(), Imeas, s_d, b_d, mask, batch)
             ctx.save_for_backward(gO, gP)
         else:
-            loss = plan.loss(O.detach(), P.detach(), Imeas, sigma, bg, mask, batch)
+            loss = plan.loss(O.detach(), P.detach(), Imeas, s_d, b_d, mask, batch)
         return loss.reshape(())
 
     @staticmethod
     def backward(ctx, grad_out):
-        gO, gP = ctx.saved_tensors
+        saved = ctx.saved_tensors
         s = grad_out.to(torch.float32)
-        return gO * s, gP * s, None, None, None, None, None, None
+        gO, gP = saved[0] * s, saved[1] * s
+        gs = gb = None
+        if len(saved) == 4:
+            gs = saved[2] * s if ctx.needs_input_grad[4] else None
+            gb = saved[3] * s if ctx.needs_input_grad[5] else None
+        return gO, gP, None, None, gs, gb, None, None
 
 
 def ptycho_loss(O, P, plan: Plan, Imeas, sigma=None, bg=None, mask=None, batch=None):
-    """Differentiable FP64 loss of complex64 parameters O (packed) and P ([L, M, F, F])."""
+    """Differentiable FP64 loss of complex64 parameters O (packed) and P ([L, M, F, F]),
+    and of the power coefficients sigma ([J]) and background bg ([F, F]) when they require
+    a gradient."""
     return PtychoLoss.apply(O, P, plan, Imeas, sigma, bg, mask, batch)

@@ -19,6 +19,8 @@
 //   k_obj_grad  grad O_l tile += sum over the batch's overlapping patches and the chunk's
 //               modes of S (each object tile is owned by one thread block: deterministic)
 //   k_loss_reduce  fixed-order FP64 sum of the per-block loss partials
+//   k_sigma_grad, k_bg_accum, k_sum_sets  gradients of the power coefficients and of the
+//               background (optional outputs of the adjoint)
 //   k_adam      Adam on the real and imaginary parts of O and P
 #pragma once
 #include "fft_regs.cuh"
@@ -278,6 +280,7 @@ struct LossArgs {
   int loss_kind;                 // 0 amplitude, 1 Poisson
   float* D;                      // [B][F][F] mask * dL/dI (camera grid), null if not needed
   double* loss_part;             // [nbatch][F*F/256] or null
+  double* sig_part;              // [nbatch][F*F/256] sums of D * (remapped sum |Psi|^2), or null
   float* I_pred;                 // [J][F][F] or null
   int remap;
 };
@@ -320,26 +323,34 @@ k_loss(KArgs a, LossArgs la) {
   const int j = batch_pos(a, i);                     // uniform over the block
   if (j < 0) {
     if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = 0.0;
+    if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = 0.0;
     if (la.D) la.D[(long long)b * FF + q] = 0.f;
     return;
   }
   const float* Ip = la.Ipart + (long long)b * a.G * FF;
-  float Ic = 0.f;
+  float Is = 0.f, Ib = 0.f;                          // field part and background part of the prediction
   bool valid = true;
   if (la.remap) {
     const int u = la.tap_base[q];
     valid = u >= 0;
     if (valid) {
       const float2 w = la.tap_w[q];
-      const float i00 = model_I(Ip, la.bg, a.G, FF, u), i01 = model_I(Ip, la.bg, a.G, FF, u + 1);
-      const float i10 = model_I(Ip, la.bg, a.G, FF, u + F), i11 = model_I(Ip, la.bg, a.G, FF, u + F + 1);
-      Ic = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
+      const float i00 = model_I(Ip, nullptr, a.G, FF, u), i01 = model_I(Ip, nullptr, a.G, FF, u + 1);
+      const float i10 = model_I(Ip, nullptr, a.G, FF, u + F), i11 = model_I(Ip, nullptr, a.G, FF, u + F + 1);
+      Is = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
+      if (la.bg) {
+        const float b00 = __ldg(la.bg + u), b01 = __ldg(la.bg + u + 1);
+        const float b10 = __ldg(la.bg + u + F), b11 = __ldg(la.bg + u + F + 1);
+        Ib = (1.f - w.x) * ((1.f - w.y) * b00 + w.y * b01) + w.x * ((1.f - w.y) * b10 + w.y * b11);
+      }
     }
   } else {
-    Ic = model_I(Ip, la.bg, a.G, FF, q);
+    Is = model_I(Ip, nullptr, a.G, FF, q);
+    if (la.bg) Ib = __ldg(la.bg + q);
   }
+  const float Ic = Is + Ib;
   if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
-  double term = 0.0;
+  double term = 0.0, sterm = 0.0;
   if (la.D || la.loss_part) {
     bool use = valid;
     if (la.mask) use = use && (la.mask[(la.mask_per_frame ? (long long)j * FF : 0) + q] != 0);
@@ -357,6 +368,19 @@ k_loss(KArgs a, LossArgs la) {
       }
     }
     if (la.D) la.D[(long long)b * FF + q] = d;
+    sterm = (double)(d * Is);
+  }
+  if (la.sig_part) {                                  // before the loss reduction reuses red
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sterm += __shfl_down_sync(0xffffffffu, sterm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sterm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int wi = 0; wi < kLossThreads / 32; ++wi) sum += red[wi];
+      la.sig_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = sum;
+    }
+    __syncthreads();
   }
   if (la.loss_part) {
 #pragma unroll
@@ -397,6 +421,20 @@ k_remap_adj(KArgs a, AdjArgs aa) {
   float gv = 0.f;
   for (int e = e0; e < e1; ++e) gv = fmaf(__ldg(aa.rt_w + e), Db[__ldg(aa.rt_idx + e)], gv);
   aa.Gt[(long long)b * FF + u] = gv;
+}
+
+// Background gradient, Eq. 1 (N is added before the remap): acc[u] += sum over the batch of
+// G[b][u] (R^T D, or D without the remap), in batch order.   grid (F*F/256)
+template <int F>
+__global__ void __launch_bounds__(256)
+k_bg_accum(const float* __restrict__ G, int nb, float* __restrict__ acc) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int FF = F * F;
+  const int u = blockIdx.x * 256 + threadIdx.x;
+  float s = acc[u];
+  for (int b = 0; b < nb; ++b) s += G[(long long)b * FF + u];
+  acc[u] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -656,6 +694,9 @@ k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
 // loss reduction and Adam (defined in ptycho_capi.cu)
 // ---------------------------------------------------------------------------------------
 __global__ void k_loss_reduce(const double* __restrict__ part, long long n, double* out);
+__global__ void k_sigma_grad(const int32_t* __restrict__ bidx, int nbatch, int J, const double* __restrict__ part,
+                             int nblk, const float* __restrict__ sigma, float* __restrict__ g);
+__global__ void k_sum_sets(const float* __restrict__ acc, int nsets, long long n, float* __restrict__ out);
 __global__ void k_tick(int* t);
 __global__ void k_adam_dev(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m,
                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,

@@ -92,6 +92,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.loss_kind = p.loss_kind;
   la.D = grad ? p.d_D : nullptr;
   la.loss_part = need_loss ? p.d_loss_part : nullptr;
+  la.sig_part = grad && c.g_sigma ? p.d_sig_part : nullptr;
   la.I_pred = c.kind == CallKind::Forward ? c.I_pred : nullptr;
   la.remap = p.remap;
 
@@ -109,6 +110,8 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   if (grad) {
     if (cudaMemsetAsync(c.gO, 0, sizeof(float2) * p.O_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
     if (cudaMemsetAsync(c.gP, 0, sizeof(float2) * p.P_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
+    if (c.g_bg && cudaMemsetAsync(p.d_gbg_set, 0, sizeof(float) * p.nsets * FF, st) != cudaSuccess)
+      return PTYCHO_ECUDA;
   }
   const int LM = p.L * p.M;
   const dim3 row_blk(RowCfg<F>::threads), col_blk(ColCfg<F>::threads);
@@ -176,6 +179,9 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(FF / kLossThreads, a.nb), kLossThreads, 0, cs, a, la));
     if (!grad) continue;
     if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_remap_adj<F>, dim3(FF / 256, a.nb), 256, 0, cs, a, aa));
+    if (c.g_bg)                                       // per-set background-gradient sum, batch order
+      PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_bg_accum<F>, dim3(FF / 256), 256, 0, cs,
+                                              (const float*)(p.remap ? aa.Gt : aa.D), a.nb, p.d_gbg_set + set * FF));
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
@@ -215,6 +221,14 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
         cudaStreamWaitEvent(st, p.ev_join[i - 1], 0) != cudaSuccess)
       return PTYCHO_ECUDA;
   }
+  if (grad && c.g_sigma)
+    PTY_LAUNCH(p, kLossReduce, st,
+               launch_pdl(k_sigma_grad, dim3((p.J + 255) / 256), 256, 0, st, (const int32_t*)c.bidx, c.nbatch, p.J,
+                          (const double*)p.d_sig_part, FF / kLossThreads, c.sigma, c.g_sigma));
+  if (grad && c.g_bg)
+    PTY_LAUNCH(p, kLossReduce, st,
+               launch_pdl(k_sum_sets, dim3(FF / 256), 256, 0, st, (const float*)p.d_gbg_set, nsets, (long long)FF,
+                          c.g_bg));
   if (need_loss) {
     double* out = c.loss;
     if (out) {

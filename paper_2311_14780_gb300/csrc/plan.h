@@ -51,6 +51,10 @@ struct ptycho_plan {
   float* d_D = nullptr;                        // [nsets][B][F][F]
   float* d_Gt = nullptr;                       // [nsets][B][F][F] R^T D (remap only)
   double* d_loss_part = nullptr;
+  double* d_sig_part = nullptr;                // [J][F*F/256] sigma-gradient partials
+  float* d_gbg_set = nullptr;                  // [nsets][F][F] background-gradient accumulators
+  float* d_gsig = nullptr;                     // [J] sigma gradient (ptycho_step)
+  float* d_gbg = nullptr;                      // [F][F] background gradient (ptycho_step)
   float2* d_gO = nullptr;
   float2* d_gP = nullptr;
   int* d_status = nullptr;                     // device status word, see ptycho_plan_status
@@ -87,6 +91,8 @@ struct CallArgs {
   float* I_pred;
   float2* gO;
   float2* gP;
+  float* g_sigma;          // [J] or null
+  float* g_bg;             // [F][F] or null
   double* loss;
 };
 

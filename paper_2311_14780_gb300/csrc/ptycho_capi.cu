@@ -27,6 +27,38 @@ __global__ void __launch_bounds__(256) k_loss_reduce(const double* __restrict__ 
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// Gradient of the power coefficients.  sigma_j multiplies every exit wave of frame j (f1),
+// and the DFT is unitary, so sum_r conj(psi) chi = 2 sum_k G_k |Psi_k|^2 and
+// dL/dsigma_j = (2 / sigma_j) sum over the camera grid of D * (R sum_lm |Psi_lm|^2), the
+// quantity the loss kernel left per block in part.  One thread per position j sums, in
+// entry order, the partials of every call entry i with bidx[i] = j; positions outside the
+// call (and sigma_j = 0, where the derivative vanishes) get 0.
+__global__ void __launch_bounds__(256)
+k_sigma_grad(const int32_t* __restrict__ bidx, int nbatch, int J, const double* __restrict__ part, int nblk,
+             const float* __restrict__ sigma, float* __restrict__ g) {
+  pdl_wait();
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  if (j >= J) return;
+  double s = 0.0;
+  for (int i = 0; i < nbatch; ++i) {
+    if (__ldg(bidx + i) != j) continue;
+    for (int k = 0; k < nblk; ++k) s += part[(long long)i * nblk + k];
+  }
+  const float sj = sigma ? __ldg(sigma + j) : 1.0f;
+  g[j] = sj != 0.f ? (float)(2.0 * s / (double)sj) : 0.f;
+}
+
+// out[u] = sum over the scratch sets, in set order, of acc[set][u].
+__global__ void __launch_bounds__(256)
+k_sum_sets(const float* __restrict__ acc, int nsets, long long n, float* __restrict__ out) {
+  pdl_wait();
+  for (long long u = blockIdx.x * 256ll + threadIdx.x; u < n; u += (long long)gridDim.x * 256) {
+    float s = 0.f;
+    for (int k = 0; k < nsets; ++k) s += acc[(long long)k * n + u];
+    out[u] = s;
+  }
+}
+
 // Adam (Kingma & Ba) on real parameters; c1, c2 are the bias corrections 1/(1-beta^t).
 __global__ void __launch_bounds__(256)
 k_adam(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
@@ -130,7 +162,8 @@ void free_plan(ptycho_plan* p) {
     }
   }
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
-                  p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status};
+                  p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
+                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -381,6 +414,10 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->nsets * p->B * p->G * FF);
   rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->nsets * p->B * FF);
   rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / ptycho::kLossThreads));
+  rc = rc ? rc : dalloc(p, &p->d_sig_part, (long long)g->J * (FF / ptycho::kLossThreads));
+  rc = rc ? rc : dalloc(p, &p->d_gbg_set, (long long)p->nsets * FF);
+  rc = rc ? rc : dalloc(p, &p->d_gsig, g->J);
+  rc = rc ? rc : dalloc(p, &p->d_gbg, FF);
   rc = rc ? rc : dalloc(p, &p->d_gO, p->O_numel);
   rc = rc ? rc : dalloc(p, &p->d_gP, p->P_numel);
   rc = rc ? rc : dalloc(p, &p->d_status, 1);
@@ -535,6 +572,14 @@ int ptycho_loss(ptycho_plan_t* p, const float* O, const float* P, const float* s
 int ptycho_adjoint(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
                    const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
                    int nbatch, float* gO, float* gP, double* loss_dev, void* stream) {
+  return ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch, gO, gP, nullptr,
+                           nullptr, loss_dev, stream);
+}
+
+int ptycho_adjoint_ex(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
+                      const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
+                      int nbatch, float* gO, float* gP, float* g_sigma, float* g_bg, double* loss_dev,
+                      void* stream) {
   if (!p || !O || !P || !I_meas || !gO || !gP) return PTYCHO_EINVAL;
   int rc = check_device(p);
   if (rc) return rc;
@@ -549,22 +594,29 @@ int ptycho_adjoint(ptycho_plan_t* p, const float* O, const float* P, const float
   c.mask_per_frame = mask_per_frame ? 1 : 0;
   c.gO = reinterpret_cast<float2*>(gO);
   c.gP = reinterpret_cast<float2*>(gP);
+  c.g_sigma = g_sigma;
+  c.g_bg = g_bg;
   c.loss = loss_dev;
   rc = fill_batch(p, c, batch_idx, nbatch);
   if (rc) return rc;
   return dispatch(p, c, (cudaStream_t)stream);
 }
 
-int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, const float* sigma, const float* bg,
+int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* sigma, float* bg,
                 const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
                 int nbatch, double* loss_dev, void* stream) {
   if (!p || !s || !O || !P || !I_meas || !s->mO || !s->vO || !s->mP || !s->vP) return PTYCHO_EINVAL;
   if (!(s->beta1 >= 0.f && s->beta1 < 1.f && s->beta2 >= 0.f && s->beta2 < 1.f && s->eps >= 0.f)) return PTYCHO_EINVAL;
-  int rc = ptycho_adjoint(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
-                          reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP), loss_dev, stream);
+  const bool opt_sigma = s->lr_sigma > 0.f, opt_bg = s->lr_bg > 0.f;
+  if (opt_sigma && (!sigma || !s->m_sigma || !s->v_sigma)) return PTYCHO_EINVAL;
+  if (opt_bg && (!bg || !s->m_bg || !s->v_bg)) return PTYCHO_EINVAL;
+  int rc = ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
+                             reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP),
+                             opt_sigma ? p->d_gsig : nullptr, opt_bg ? p->d_gbg : nullptr, loss_dev, stream);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;
+  const long long FF = (long long)p->F * p->F;
   const int grid = 4 * p->sms;
   if (s->t_dev) {
     // device step counter: the update can be captured once and replayed
@@ -577,6 +629,16 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, const fl
     ptycho::k_adam_dev<<<grid, 256, 0, st>>>(P, reinterpret_cast<const float*>(p->d_gP), s->mP, s->vP, nP, s->lr_P,
                                              s->beta1, s->beta2, s->eps, s->t_dev);
     p->last_launches += 2;
+    if (opt_sigma) {
+      ptycho::k_adam_dev<<<(p->J + 255) / 256, 256, 0, st>>>(sigma, p->d_gsig, s->m_sigma, s->v_sigma, p->J,
+                                                             s->lr_sigma, s->beta1, s->beta2, s->eps, s->t_dev);
+      ++p->last_launches;
+    }
+    if (opt_bg) {
+      ptycho::k_adam_dev<<<(int)((FF + 255) / 256), 256, 0, st>>>(bg, p->d_gbg, s->m_bg, s->v_bg, FF, s->lr_bg,
+                                                                   s->beta1, s->beta2, s->eps, s->t_dev);
+      ++p->last_launches;
+    }
     if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
     ptycho::prof_end(*p, ev, st);
     return PTYCHO_OK;
@@ -596,6 +658,17 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, const fl
   ++p->last_launches;
   if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
   ptycho::prof_end(*p, ev, st);
+  if (opt_sigma) {
+    ptycho::k_adam<<<(p->J + 255) / 256, 256, 0, st>>>(sigma, p->d_gsig, s->m_sigma, s->v_sigma, p->J, s->lr_sigma,
+                                                       s->beta1, s->beta2, s->eps, (float)c1, (float)c2);
+    ++p->last_launches;
+  }
+  if (opt_bg) {
+    ptycho::k_adam<<<(int)((FF + 255) / 256), 256, 0, st>>>(bg, p->d_gbg, s->m_bg, s->v_bg, FF, s->lr_bg, s->beta1,
+                                                             s->beta2, s->eps, (float)c1, (float)c2);
+    ++p->last_launches;
+  }
+  if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
   return PTYCHO_OK;
 }
 

@@ -350,3 +350,135 @@ def test_pipeline_variants(dev, flags, F):
     plan = case.plan(flags=flags, scratch_bytes=5 * 6 * F * F * 8)    # several batches in flight
     assert_ok(check_all(case, plan))
     plan.close()
+
+
+# ---------------------------------------------------------------------------------------
+# gradients of the power coefficients sigma_j and the background N (Eq. 1; the paper lists
+# both among the optimised variables)
+# ---------------------------------------------------------------------------------------
+
+def _sigma_bg_errors(case, plan, frames=None):
+    batch = None if frames is None else torch.as_tensor(np.asarray(frames, np.int32), device=case.dev)
+    La, gO, gP, gs, gb = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
+    Lr, gsr, gbr = orc.gradient_sigma_bg(case.O0, case.P0, case.w.pos, case.Ih, case.loss, case.eps, case.sigma,
+                                         case.bg, case.mask, case.taps, frames)
+    _, gOr, gPr = case.oracle_grad(frames)
+    gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    return dict(L=abs(float(La.item()) - Lr) / abs(Lr), gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr),
+                gs=rel(gs.cpu().numpy(), gsr), gb=rel(gb.cpu().numpy(), gbr), gs_gpu=gs.cpu().numpy(),
+                status=plan.status())
+
+
+@pytest.mark.parametrize("remap,loss,mask_kind", [(True, "poisson", "frame"), (False, "amplitude", None),
+                                                   (True, "amplitude", "shared"), (False, "poisson", "frame")])
+def test_sigma_background_gradients(dev, remap, loss, mask_kind):
+    w = syn.tiny_workload(F=64, L=2, M=3, n_side=3, step=10, seed=31, remap=remap, loss=loss, with_sigma=True,
+                          with_bg=True)
+    case = Case(w, dev, z=strong_z(64), mask_kind=mask_kind, seed=5)
+    plan = case.plan()
+    e = _sigma_bg_errors(case, plan)
+    assert e["status"] == 0 and e["L"] < TOL_L, e
+    for k in ("gO", "gP", "gs", "gb"):
+        assert e[k] < TOL_G, (k, e)
+    plan.close()
+
+
+@pytest.mark.parametrize("F", [64, 256])
+def test_sigma_background_gradients_batches_and_subset(dev, F):
+    """Several position batches on overlapping streams, recompute mode and a position subset in
+    any order: sigma's gradient is 0 outside the subset and the background's sums the subset."""
+    w = syn.tiny_workload(F=F, L=2, M=2, n_side=4, step=F // 8, seed=33, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(F), mask_kind="frame", seed=9)
+    frames = [11, 3, 0, 14, 7]
+    for kw in (dict(scratch_bytes=2 * 4 * F * F * 8, overlap=3), dict(scratch_bytes=F * F * 8)):
+        plan = case.plan(**kw)
+        for fr in (None, frames):
+            e = _sigma_bg_errors(case, plan, fr)
+            assert e["status"] == 0 and e["L"] < TOL_L, (kw, fr, e)
+            for k in ("gO", "gP", "gs", "gb"):
+                assert e[k] < TOL_G, (kw, fr, k, e)
+            if fr is not None:
+                outside = np.setdiff1d(np.arange(w.J), fr)
+                assert np.all(e["gs_gpu"][outside] == 0.0)
+        plan.close()
+
+
+def test_sigma_gradient_without_sigma_and_at_zero(dev):
+    """sigma NULL means all ones; a zero sigma_j has a zero derivative (I is quadratic in it)."""
+    w = syn.tiny_workload(F=64, L=1, M=2, n_side=3, step=10, seed=35, remap=False, loss="amplitude", with_bg=True)
+    case = Case(w, dev, seed=2)
+    plan = case.plan()
+    _, _, _, gs, _ = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    _, gsr, _ = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, None, case.bg)
+    assert rel(gs.cpu().numpy(), gsr) < TOL_G
+    sig = torch.ones(w.J, dtype=torch.float32, device=dev)
+    sig[4] = 0.0
+    _, _, _, gs0, _ = plan.adjoint_ex(case.O, case.P, case.Im, sig, case.bg_t)
+    assert float(gs0[4].item()) == 0.0
+    _, gsr0, _ = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps,
+                                       sig.cpu().numpy().astype(np.float64), case.bg)
+    assert rel(gs0.cpu().numpy(), gsr0) < TOL_G
+    plan.close()
+
+
+@pytest.mark.parametrize("device_counter", [False, True])
+def test_step_updates_sigma_and_background(dev, device_counter):
+    """ptycho_step with lr_sigma, lr_bg > 0 against the oracle's Adam step on O, P, sigma, bg."""
+    from paper_2311_14780_gb300 import AdamState
+    w = syn.tiny_workload(F=64, L=2, M=2, n_side=3, step=10, seed=37, remap=True, loss="poisson", with_sigma=True,
+                          with_bg=True)
+    case = Case(w, dev, z=strong_z(64), seed=6)
+    plan = case.plan()
+    lr = dict(lr_O=1e-2, lr_P=1e-1, lr_sigma=1e-2, lr_bg=1e-1)
+    st = AdamState(plan, lr["lr_O"], lr["lr_P"], device_counter=device_counter, lr_sigma=lr["lr_sigma"],
+                   lr_bg=lr["lr_bg"])
+    O, P = case.O.clone(), case.P.clone()
+    sig, bg = case.sig_t.clone(), case.bg_t.clone()
+    frames = [0, 5, 8, 2]
+    bt = torch.as_tensor(np.asarray(frames, np.int32), device=dev)
+    ost = orc.AdamState([o.shape for o in case.O0], case.P0.shape)
+    ms, vs = np.zeros(w.J), np.zeros(w.J)
+    mb, vb = np.zeros((w.F, w.F)), np.zeros((w.F, w.F))
+    On, Pn, sn, bn = case.O0, case.P0, case.sigma, case.bg
+    for it in range(2):
+        L = float(plan.step(st, O, P, case.Im, sig, bg, batch=bt).item())
+        Lr, On, Pn, sn, bn = orc.step_sigma_bg(On, Pn, sn, bn, w.pos, case.Ih, case.loss, case.eps, ost, ms, vs,
+                                               mb, vb, lr["lr_O"], lr["lr_P"], lr["lr_sigma"], lr["lr_bg"],
+                                               taps=case.taps, frames=frames)
+        assert abs(L - Lr) < TOL_L * abs(Lr), (it, L, Lr)
+        dO = O.cpu().numpy() - np.concatenate([o.reshape(-1) for o in case.O0])
+        dOr = np.concatenate([(a - b).reshape(-1) for a, b in zip(On, case.O0)])
+        assert rel(dO, dOr) < 1e-4, it
+        assert rel(P.cpu().numpy() - case.P0, Pn - case.P0) < 1e-4, it
+        assert rel(sig.cpu().numpy() - case.sigma, sn - case.sigma) < 1e-4, it
+        assert rel(bg.cpu().numpy() - case.bg, bn - case.bg) < 1e-4, it
+        # positions outside the batch: zero gradient, but Adam's momentum still moves them after step 1
+        if it == 0:
+            outside = np.setdiff1d(np.arange(w.J), frames)
+            assert np.all(sig.cpu().numpy()[outside] == np.asarray(case.sig_t.cpu().numpy())[outside])
+    plan.close()
+
+
+def test_autograd_sigma_background(dev):
+    """torch.autograd through sigma and bg: a directional derivative vs central differences."""
+    from paper_2311_14780_gb300.autograd import ptycho_loss
+    w = syn.tiny_workload(F=64, L=2, M=2, n_side=3, step=10, seed=39, remap=True, loss="amplitude", with_sigma=True,
+                          with_bg=True)
+    case = Case(w, dev, z=strong_z(64), seed=4)
+    plan = case.plan()
+    sig = case.sig_t.clone().requires_grad_(True)
+    bg = case.bg_t.clone().requires_grad_(True)
+    L = ptycho_loss(case.O, case.P, plan, case.Im, sig, bg)
+    L.backward()
+    g = torch.Generator(device="cpu").manual_seed(1)
+    ds = torch.randn(sig.shape, generator=g).to(dev)
+    db = torch.randn(bg.shape, generator=g).to(dev)
+    an = float((torch.dot(sig.grad, ds) + torch.dot(bg.grad.reshape(-1), db.reshape(-1))).item())
+    with torch.no_grad():
+        h = 1e-3
+        Lp = float(ptycho_loss(case.O, case.P, plan, case.Im, sig + h * ds, bg + h * db).item())
+        Lm = float(ptycho_loss(case.O, case.P, plan, case.Im, sig - h * ds, bg - h * db).item())
+    fd = (Lp - Lm) / (2 * h)
+    assert abs(fd - an) < 2e-3 * abs(an), (fd, an)
+    plan.close()
