@@ -61,12 +61,33 @@ extern "C" {
  * TMA / NO_TMA: the column passes stage each mode's column block in shared memory with
  *   bulk tensor copies (TMA) / read S with ordinary loads.  Default: TMA for F >= 512,
  *   where it measured faster; below that the larger shared-memory footprint costs more
- *   occupancy than the copies save.  NO_TMA wins when both are given. */
+ *   occupancy than the copies save.  NO_TMA wins when both are given.
+ * UNFUSED_ROW_ADJ: one block of the adjoint row pass per probe mode, each mode's object-
+ *   gradient row left in the scratch for the object-gradient kernel (always the case for
+ *   F = 512).  The default for F <= 256, whenever all modes of a position fit the scratch and
+ *   T*M <= 256 (T = 4, 8, 16 threads per row for F = 64, 128, 256), takes all modes of a
+ *   wavelength per block: the probe rows
+ *   stay in shared memory for the batch and the object-gradient rows are summed over the
+ *   modes before they are written.
+ * STAGED_COLUMNS: whenever all modes of a position fit the scratch, run each column block over
+ *   all modes of W columns of one position, copying the next mode's columns into shared memory
+ *   (cp.async, double-buffered) while the current one is transformed (one intensity slice, no
+ *   mode groups).  Measured slower than the default mode groups on every benchmark workload
+ *   (fewer warps per SM); NARROW_COLUMNS takes 4 columns per block instead of 8.
+ * FUSED_ROW_FWD: the forward row pass over all modes of a wavelength per block, the probe row
+ *   in registers and the next position's object rows prefetched (cp.async).  Measured slower
+ *   than the default one-position-per-block pass.
+ * NO_PDL: launch without programmatic dependent launch. */
 #define PTYCHO_FLAG_RECOMPUTE_COLUMNS 1
 #define PTYCHO_FLAG_OBJ_GRAD_ATOMIC 2
 #define PTYCHO_FLAG_KEEP_PSI 4
 #define PTYCHO_FLAG_NO_TMA 8
 #define PTYCHO_FLAG_TMA 16
+#define PTYCHO_FLAG_UNFUSED_ROW_ADJ 32
+#define PTYCHO_FLAG_STAGED_COLUMNS 64
+#define PTYCHO_FLAG_NARROW_COLUMNS 128
+#define PTYCHO_FLAG_FUSED_ROW_FWD 256
+#define PTYCHO_FLAG_NO_PDL 512
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */

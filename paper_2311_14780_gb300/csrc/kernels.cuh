@@ -30,6 +30,8 @@ namespace ptycho {
 
 constexpr int kMaxL = 16;
 constexpr int kLossThreads = 256;
+constexpr int kLossPx = 4;       // camera pixels per thread in the loss kernel
+template <int F> __host__ __device__ constexpr int loss_blocks() { return F * F / (kLossThreads * kLossPx); }
 constexpr int kTile = 32;        // object-gradient tile side
 constexpr int kMaxB = 512;       // positions per batch (upper bound)
 
@@ -139,13 +141,38 @@ k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   }
 }
 
+// After the G mode-group blocks of (position b, column block) have written their intensity
+// slices, the last of them to finish (a counter per (b, column block), reset for the next
+// launch) adds the G slices in group order into slice 0, so that later passes read one slice.
+// The order of the sum does not depend on which block comes last.
+template <int F, int W>
+__device__ __forceinline__ void sum_group_slices(float* __restrict__ Ipart, int* __restrict__ cnt, int G, int b,
+                                                 int col0) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(cnt + b * (F / W) + col0 / W, 1) == G - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int cc0 = (col0 + F / 2) & (F - 1);           // the block's W centred columns are contiguous
+  float* base = Ipart + (long long)b * G * F * F + cc0;
+  for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
+    const int row = e / W, c = e % W;
+    float sum = __ldcg(base + row * F + c);
+    for (int g = 1; g < G; ++g) sum += __ldcg(base + (long long)g * F * F + row * F + c);
+    base[row * F + c] = sum;
+  }
+  if (threadIdx.x == 0) cnt[b * (F / W) + col0 / W] = 0;
+}
+
 // ---------------------------------------------------------------------------------------
 // forward column pass: column DFT (second half of f4), |Psi|^2 summed over a mode group
 // grid (F/W, G, nb)
 // ---------------------------------------------------------------------------------------
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
-k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk) {
+k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk, int* __restrict__ cnt) {
   pdl_wait();
   pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
@@ -179,6 +206,7 @@ k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_
     if (!first_chunk) val += dst[rc * F + cc];
     dst[rc * F + cc] = val;
   }
+  if (cnt && a.G > 1) sum_group_slices<F, W>(Ipart, cnt, a.G, b, blockIdx.x * W);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -191,9 +219,18 @@ template <int F> struct ColTma {
   static constexpr int W = ColCfg<F>::W;
   static constexpr int box_rows = F < 256 ? F : 256;
   static constexpr int stage_bytes = F * W * (int)sizeof(float2);
-  static constexpr int smem_fwd = stage_bytes + ColCfg<F>::smem_xch + 16;
+  // + 128: the stage is placed on a 128-byte boundary inside the dynamic shared memory (whose
+  // start moves with the kernel's static shared variables)
+  static constexpr int smem_fwd = stage_bytes + ColCfg<F>::smem_xch + 16 + 128;
   static constexpr int smem_adj = smem_fwd + F * W * (int)sizeof(float);
 };
+
+// The first 128-byte-aligned address (in the shared window) at or after p: the destination of
+// a bulk tensor copy must be 128-byte aligned.
+__device__ __forceinline__ float2* align_tma_stage(unsigned char* p) {
+  const uint32_t pad = (128u - (smem_addr(p) & 127u)) & 127u;
+  return reinterpret_cast<float2*>(p + pad);
+}
 
 template <int F>
 __device__ __forceinline__ void col_tma_issue(float2* stage, const CUtensorMap* map, int col0, int row0, uint64_t* bar) {
@@ -208,11 +245,12 @@ __device__ __forceinline__ void col_tma_issue(float2* stage, const CUtensorMap* 
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
 k_col_fwd_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, float* __restrict__ Ipart, KArgs a,
-              int first_chunk) {
+              int first_chunk, int* __restrict__ cnt) {
   pdl_wait();
   pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
-  extern __shared__ __align__(128) float2 smem[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* smem = align_tma_stage(smem_raw);
   float2* stage = smem;
   float2* xch = smem + F * W;
   uint64_t* bar = reinterpret_cast<uint64_t*>(xch + W * Xch<F>::region_cols);
@@ -262,6 +300,88 @@ k_col_fwd_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, f
     if (!first_chunk) val += dst[rc * F + cc];
     dst[rc * F + cc] = val;
   }
+  if (cnt && a.G > 1) sum_group_slices<F, W>(Ipart, cnt, a.G, b, blockIdx.x * W);
+}
+
+// ---------------------------------------------------------------------------------------
+// Staged column passes (one mode chunk holding every mode, one group: G = 1).  A block
+// takes W columns of one position and runs over all its modes; the W x F column block of
+// the next mode is copied into shared memory (cp.async, double-buffered) while the current
+// one is transformed, so a block always has one mode's data in flight.
+// grid (F/W, nb), block W*T
+// ---------------------------------------------------------------------------------------
+template <int F, int WN = 0> struct ColSCfg {
+  static constexpr int T = FftShape<F>::N1;
+  static constexpr int W = WN > 0 ? WN : (F >= 256 ? 8 : 128 / T);   // columns per block
+  static constexpr int threads = W * T;
+  static constexpr int stage = F * W;                // float2 per stage
+  // exchange-region stride: a warp holds columns c < W and 32/W threads t of each; with the
+  // stride = 32/W (mod 16) the offsets c*R + t fall on every 8-byte bank pair exactly twice
+  // (two wavefronts, the minimum for 32 x 8 bytes); W >= 32 only needs an odd stride
+  static constexpr int R = W >= 32 ? (Xch<F>::base | 1)
+                                   : Xch<F>::base + (((32 / W) - Xch<F>::base) % 16 + 16) % 16;
+  static constexpr int smem_fwd = (2 * stage + W * R) * (int)sizeof(float2);
+  static constexpr int smem_adj = smem_fwd + F * W * (int)sizeof(float);
+};
+
+// Issue the copies of mode slot cm's W x F column block (from column col0) into dst.
+template <int F, int WN>
+__device__ __forceinline__ void col_prefetch(const float2* __restrict__ Sb, int cm, int col0, float2* dst) {
+  constexpr int W = ColSCfg<F, WN>::W, CH = F * W / 2;  // 16-byte chunks
+  const float2* src = Sb + (long long)cm * F * F + col0;
+  for (int e = threadIdx.x; e < CH; e += ColSCfg<F, WN>::threads) {
+    const int row = e / (W / 2), cc = (e % (W / 2)) * 2;
+    cp_async16(dst + row * W + cc, src + (long long)row * F + cc);
+  }
+  cp_async_commit();
+}
+
+template <int F, bool STORE, int WN>
+__global__ void __launch_bounds__(ColSCfg<F, WN>::threads)
+k_col_fwd_s(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColSCfg<F, WN>::W, ST = ColSCfg<F, WN>::stage;
+  extern __shared__ __align__(16) float2 smem[];
+  float2* stage = smem;                               // [2][F][W]
+  float2* xch = smem + 2 * ST;
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int col0 = blockIdx.x * W, col = col0 + c;
+  const int b = blockIdx.y;
+  const int nm = a.chunk_len;
+  float2* Sb = S + (long long)b * a.C * F * F;
+  float acc[N2];
+#pragma unroll
+  for (int i = 0; i < N2; ++i) acc[i] = 0.f;
+  const float inv = 1.0f / (float)F;
+  if (nm > 0) col_prefetch<F, WN>(Sb, 0, col0, stage);
+  for (int cm = 0; cm < nm; ++cm) {
+    const float2* cur = stage + (cm & 1) * ST;
+    if (cm + 1 < nm) {
+      col_prefetch<F, WN>(Sb, cm + 1, col0, stage + ((cm + 1) & 1) * ST);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = cur[(t + N1 * n2) * W + c];
+    fft_fwd_I2O<F>(v, t, xch + c * ColSCfg<F, WN>::R, a.tw, BlockSync{});   // its first barrier frees cur
+    float2* base = Sb + (long long)cm * F * F + col;
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) {
+      acc[sl] = fmaf(v[sl].x, v[sl].x, fmaf(v[sl].y, v[sl].y, acc[sl]));
+      if (STORE) base[(long long)idxO<F>(t, sl) * F] = cscale(v[sl], inv);
+    }
+  }
+  float* dst = Ipart + (long long)b * F * F;
+  const int cc = (col + F / 2) & (F - 1);
+#pragma unroll
+  for (int sl = 0; sl < N2; ++sl) {
+    const int rc = (idxO<F>(t, sl) + F / 2) & (F - 1);
+    dst[rc * F + cc] = acc[sl] * (inv * inv);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -279,10 +399,11 @@ struct LossArgs {
   float eps;
   int loss_kind;                 // 0 amplitude, 1 Poisson
   float* D;                      // [B][F][F] mask * dL/dI (camera grid), null if not needed
-  double* loss_part;             // [nbatch][F*F/256] or null
-  double* sig_part;              // [nbatch][F*F/256] sums of D * (remapped sum |Psi|^2), or null
+  double* loss_part;             // [nbatch][loss_blocks] or null
+  double* sig_part;              // [nbatch][loss_blocks] sums of D * (remapped sum |Psi|^2), or null
   float* I_pred;                 // [J][F][F] or null
   int remap;
+  int Gsum;                      // intensity slices to add (1 once the column pass has summed them)
 };
 
 __device__ __forceinline__ float model_I(const float* Ip, const float* bg, int G, int FF, int u) {
@@ -310,94 +431,149 @@ __device__ __forceinline__ float poisson_term(float Ie, float Ih) {
   return Ih * f;
 }
 
+// Camera-grid prediction of one pixel q (remap: bilinear in the four model taps of q).
+// Is is the field part, Ib the background part; valid = false outside the remap's grid.
+template <int F>
+__device__ __forceinline__ void predict_pixel(const LossArgs& la, const float* Ip, int G, int q, int tb, float2 w,
+                                              float& Is, float& Ib, bool& valid) {
+  constexpr int FF = F * F;
+  Is = 0.f;
+  Ib = 0.f;
+  valid = true;
+  if (la.remap) {
+    valid = tb >= 0;
+    if (!valid) return;
+    const float i00 = model_I(Ip, nullptr, G, FF, tb), i01 = model_I(Ip, nullptr, G, FF, tb + 1);
+    const float i10 = model_I(Ip, nullptr, G, FF, tb + F), i11 = model_I(Ip, nullptr, G, FF, tb + F + 1);
+    Is = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
+    if (la.bg) {
+      const float b00 = __ldg(la.bg + tb), b01 = __ldg(la.bg + tb + 1);
+      const float b10 = __ldg(la.bg + tb + F), b11 = __ldg(la.bg + tb + F + 1);
+      Ib = (1.f - w.x) * ((1.f - w.y) * b00 + w.y * b01) + w.x * ((1.f - w.y) * b10 + w.y * b11);
+    }
+  } else {
+    Is = model_I(Ip, nullptr, G, FF, q);
+    if (la.bg) Ib = __ldg(la.bg + q);
+  }
+}
+
+// Compensated FP32 sums ("double-float": value = hi + lo).  Knuth's TwoSum gives the exact
+// rounding error of an addition, so the pair carries about twice the FP32 mantissa without
+// FP64 arithmetic (slow on this part).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo += e;
+}
+__device__ __forceinline__ void df_add_df(float& hi, float& lo, float bhi, float blo) {
+  float s, e;
+  two_sum(hi, bhi, s, e);
+  e += lo + blo;
+  hi = s + e;                                    // renormalise (Fast2Sum, |s| >= |e|)
+  lo = e - (hi - s);
+}
+// Warp-tree sum of a double-float (fixed pairing: the result does not depend on timing).
+__device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_down_sync(0xffffffffu, hi, o), bl = __shfl_down_sync(0xffffffffu, lo, o);
+    df_add_df(hi, lo, bh, bl);
+  }
+}
+
+// Each thread takes kLossPx consecutive camera pixels; the loss terms and the sigma-gradient
+// terms of a block are summed as double-floats (per thread, then a warp tree) and the eight
+// warp sums in FP64, in a fixed order, into one partial per (call entry, block).
+// grid (F*F/(kLossThreads*kLossPx), nb)
 template <int F>
 __global__ void __launch_bounds__(kLossThreads)
 k_loss(KArgs a, LossArgs la) {
   pdl_wait();
   pdl_trigger();
-  constexpr int FF = F * F;
-  __shared__ double red[kLossThreads / 32];
+  constexpr int FF = F * F, NB = loss_blocks<F>();
+  __shared__ float red[4][kLossThreads / 32];
   const int b = blockIdx.y;
   const int i = a.batch_off + b;
-  const int q = blockIdx.x * kLossThreads + threadIdx.x;
+  const int q0 = (blockIdx.x * kLossThreads + threadIdx.x) * kLossPx;
   const int j = batch_pos(a, i);                     // uniform over the block
   if (j < 0) {
-    if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = 0.0;
-    if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = 0.0;
-    if (la.D) la.D[(long long)b * FF + q] = 0.f;
+    if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * NB + blockIdx.x] = 0.0;
+    if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * NB + blockIdx.x] = 0.0;
+    if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   const float* Ip = la.Ipart + (long long)b * a.G * FF;
-  float Is = 0.f, Ib = 0.f;                          // field part and background part of the prediction
-  bool valid = true;
+  int tb[kLossPx];
+  float2 tw[kLossPx];
   if (la.remap) {
-    const int u = la.tap_base[q];
-    valid = u >= 0;
-    if (valid) {
-      const float2 w = la.tap_w[q];
-      const float i00 = model_I(Ip, nullptr, a.G, FF, u), i01 = model_I(Ip, nullptr, a.G, FF, u + 1);
-      const float i10 = model_I(Ip, nullptr, a.G, FF, u + F), i11 = model_I(Ip, nullptr, a.G, FF, u + F + 1);
-      Is = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
-      if (la.bg) {
-        const float b00 = __ldg(la.bg + u), b01 = __ldg(la.bg + u + 1);
-        const float b10 = __ldg(la.bg + u + F), b11 = __ldg(la.bg + u + F + 1);
-        Ib = (1.f - w.x) * ((1.f - w.y) * b00 + w.y * b01) + w.x * ((1.f - w.y) * b10 + w.y * b11);
-      }
-    }
+    const int4 t4 = *reinterpret_cast<const int4*>(la.tap_base + q0);
+    const float4 w01 = *reinterpret_cast<const float4*>(la.tap_w + q0);
+    const float4 w23 = *reinterpret_cast<const float4*>(la.tap_w + q0 + 2);
+    tb[0] = t4.x; tb[1] = t4.y; tb[2] = t4.z; tb[3] = t4.w;
+    tw[0] = make_float2(w01.x, w01.y); tw[1] = make_float2(w01.z, w01.w);
+    tw[2] = make_float2(w23.x, w23.y); tw[3] = make_float2(w23.z, w23.w);
   } else {
-    Is = model_I(Ip, nullptr, a.G, FF, q);
-    if (la.bg) Ib = __ldg(la.bg + q);
+#pragma unroll
+    for (int k = 0; k < kLossPx; ++k) { tb[k] = 0; tw[k] = make_float2(0.f, 0.f); }
   }
-  const float Ic = Is + Ib;
-  if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
-  double term = 0.0, sterm = 0.0;
-  if (la.D || la.loss_part) {
-    bool use = valid;
-    if (la.mask) use = use && (la.mask[(la.mask_per_frame ? (long long)j * FF : 0) + q] != 0);
-    float d = 0.f;
-    if (use) {
-      const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
-      const float Ie = Ic + la.eps;
-      if (la.loss_kind == 0) {
-        const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
-        term = (double)(diff * diff);
-        d = diff / se;
-      } else {
-        term = (double)poisson_term(Ie, Ih);
-        d = (Ie - Ih) / Ie;
+  float d[kLossPx];
+  float th = 0.f, tl = 0.f, sh = 0.f, sl = 0.f;   // double-float sums of the loss and sigma terms
+#pragma unroll
+  for (int k = 0; k < kLossPx; ++k) {
+    const int q = q0 + k;
+    float Is, Ib;
+    bool valid;
+    predict_pixel<F>(la, Ip, la.Gsum, q, tb[k], tw[k], Is, Ib, valid);
+    const float Ic = Is + Ib;
+    if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
+    d[k] = 0.f;
+    if (la.D || la.loss_part) {
+      bool use = valid;
+      if (la.mask) use = use && (la.mask[(la.mask_per_frame ? (long long)j * FF : 0) + q] != 0);
+      if (use) {
+        const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
+        const float Ie = Ic + la.eps;
+        if (la.loss_kind == 0) {
+          const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
+          df_add(th, tl, diff * diff);
+          d[k] = __fdividef(diff, se);                 // 2 ulp: ample for a gradient
+        } else {
+          df_add(th, tl, poisson_term(Ie, Ih));
+          d[k] = __fdividef(Ie - Ih, Ie);
+        }
       }
+      df_add(sh, sl, d[k] * Is);
     }
-    if (la.D) la.D[(long long)b * FF + q] = d;
-    sterm = (double)(d * Is);
   }
-  if (la.sig_part) {                                  // before the loss reduction reuses red
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sterm += __shfl_down_sync(0xffffffffu, sterm, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sterm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int wi = 0; wi < kLossThreads / 32; ++wi) sum += red[wi];
-      la.sig_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = sum;
-    }
-    __syncthreads();
+  if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(d[0], d[1], d[2], d[3]);
+  if (!la.loss_part && !la.sig_part) return;
+  df_warp_sum(th, tl);
+  df_warp_sum(sh, sl);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = th;
+    red[1][threadIdx.x >> 5] = tl;
+    red[2][threadIdx.x >> 5] = sh;
+    red[3][threadIdx.x >> 5] = sl;
   }
-  if (la.loss_part) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int wi = 0; wi < kLossThreads / 32; ++wi) sum += red[wi];
-      la.loss_part[(long long)i * (FF / kLossThreads) + blockIdx.x] = sum;
-    }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double sum = 0.0;
+    for (int wi = 0; wi < kLossThreads / 32; ++wi)
+      sum += (double)red[2 * threadIdx.x][wi] + (double)red[2 * threadIdx.x + 1][wi];
+    double* out = threadIdx.x == 0 ? la.loss_part : la.sig_part;
+    if (out) out[(long long)i * NB + blockIdx.x] = sum;
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // R^T of the tilted-plane remap: G[b][u] = sum over the camera pixels q that sample model
-// pixel u of w_uq D[b][q] (CSR rows in increasing q: a fixed order).   grid (F*F/256, nb)
+// pixel u of w_uq D[b][q] (CSR rows in increasing q: a fixed order).
 // ---------------------------------------------------------------------------------------
 struct AdjArgs {
   const float* D;                // [B][F][F] camera grid
@@ -408,6 +584,9 @@ struct AdjArgs {
   int remap;
 };
 
+// One thread per model pixel u and kRtPos positions of the batch: the CSR entries of u are
+// read once and the positions' D loads are independent.   grid (F*F/256, ceil(nb/kRtPos))
+constexpr int kRtPos = 4;
 template <int F>
 __global__ void __launch_bounds__(256)
 k_remap_adj(KArgs a, AdjArgs aa) {
@@ -415,12 +594,23 @@ k_remap_adj(KArgs a, AdjArgs aa) {
   pdl_trigger();
   constexpr int FF = F * F;
   const int u = blockIdx.x * 256 + threadIdx.x;
-  const int b = blockIdx.y;
+  const int b0 = blockIdx.y * kRtPos;
+  const int nbk = min(kRtPos, a.nb - b0);
   const int e0 = __ldg(aa.rt_ptr + u), e1 = __ldg(aa.rt_ptr + u + 1);
-  const float* Db = aa.D + (long long)b * FF;
-  float gv = 0.f;
-  for (int e = e0; e < e1; ++e) gv = fmaf(__ldg(aa.rt_w + e), Db[__ldg(aa.rt_idx + e)], gv);
-  aa.Gt[(long long)b * FF + u] = gv;
+  const float* Db = aa.D + (long long)b0 * FF;
+  float gv[kRtPos];
+#pragma unroll
+  for (int k = 0; k < kRtPos; ++k) gv[k] = 0.f;
+  for (int e = e0; e < e1; ++e) {
+    const float w = __ldg(aa.rt_w + e);
+    const int q = __ldg(aa.rt_idx + e);
+#pragma unroll
+    for (int k = 0; k < kRtPos; ++k)
+      if (k < nbk) gv[k] = fmaf(w, Db[(long long)k * FF + q], gv[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < kRtPos; ++k)
+    if (k < nbk) aa.Gt[(long long)(b0 + k) * FF + u] = gv[k];
 }
 
 // Background gradient, Eq. 1 (N is added before the remap): acc[u] += sum over the batch of
@@ -483,6 +673,60 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
   }
 }
 
+// Staged adjoint column pass (see k_col_fwd_s).   grid (F/W, nb), block W*T
+template <int F, bool STORE, int WN>
+__global__ void __launch_bounds__(ColSCfg<F, WN>::threads)
+k_col_adj_s(float2* __restrict__ S, KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColSCfg<F, WN>::W, ST = ColSCfg<F, WN>::stage;
+  extern __shared__ __align__(16) float2 smem[];
+  float2* stage = smem;                               // [2][F][W]
+  float2* xch = smem + 2 * ST;
+  float* gt = reinterpret_cast<float*>(xch + W * ColSCfg<F, WN>::R);   // [F][W]
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int col0 = blockIdx.x * W, col = col0 + c;
+  const int b = blockIdx.y;
+  const int nm = a.chunk_len;
+  float2* Sb = S + (long long)b * a.C * F * F;
+  if (nm > 0) col_prefetch<F, WN>(Sb, 0, col0, stage);
+  const float* Gb = (aa.remap ? aa.Gt : aa.D) + (long long)b * F * F;
+  const float scale = 2.0f / (float)F;
+  for (int e = threadIdx.x; e < F * W; e += ColSCfg<F, WN>::threads) {
+    const int k = e / W, ce = e % W;
+    const int u = ((k + F / 2) & (F - 1)) * F + ((col0 + ce + F / 2) & (F - 1));
+    gt[k * W + ce] = Gb[u] * scale;
+  }
+  const float inv = 1.0f / (float)F;
+  for (int cm = 0; cm < nm; ++cm) {
+    const float2* cur = stage + (cm & 1) * ST;
+    if (cm + 1 < nm) {
+      col_prefetch<F, WN>(Sb, cm + 1, col0, stage + ((cm + 1) & 1) * ST);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    float2 v[N2];
+    if (STORE) {
+#pragma unroll
+      for (int sl = 0; sl < N2; ++sl) v[sl] = cur[idxO<F>(t, sl) * W + c];
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = cur[(t + N1 * n2) * W + c];
+      fft_fwd_I2O<F>(v, t, xch + c * ColSCfg<F, WN>::R, a.tw, BlockSync{});
+#pragma unroll
+      for (int sl = 0; sl < N2; ++sl) v[sl] = cscale(v[sl], inv);
+    }
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) v[sl] = cscale(v[sl], gt[idxO<F>(t, sl) * W + c]);
+    fft_inv_O2I<F>(v, t, xch + c * ColSCfg<F, WN>::R, a.tw, BlockSync{});   // its first barrier frees cur
+    float2* base = Sb + (long long)cm * F * F + col;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) base[(long long)(t + N1 * n2) * F] = v[n2];
+  }
+}
+
 // grid (F/W, G, nb); same results as k_col_adj
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
@@ -490,7 +734,8 @@ k_col_adj_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, K
   pdl_wait();
   pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
-  extern __shared__ __align__(128) float2 smem[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* smem = align_tma_stage(smem_raw);
   float2* stage = smem;
   float2* xch = smem + F * W;
   uint64_t* bar = reinterpret_cast<uint64_t*>(xch + W * Xch<F>::region_cols);
@@ -678,6 +923,269 @@ k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
 #pragma unroll
         for (int k = 0; k < kTile / 8; ++k) acc[k] = cadd(acc[k], v[mm][k]);
     }
+  }
+  float2* g = gO + a.obj_off[l];
+#pragma unroll
+  for (int k = 0; k < kTile / 8; ++k) {
+    const int oy = oy0 + ty0 + 8 * k;
+    if (oy < H && ox < Wd) {
+      float2* p = g + (long long)oy * Wd + ox;
+      *p = cadd(*p, acc[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint row pass over all modes of one wavelength (one mode chunk holds every mode).
+// Vector v = rr*M + m of a block takes row r = blockIdx.x*rpb + rr of probe mode (l, m).
+// Per scan position of the block's split: chi = dL/dpsi by the inverse row DFT; the probe
+// gradient of (l, m, r) is summed in registers over the split's positions; the object-gradient
+// row sum_m conj(sigma P_lm) chi is formed in shared memory (modes added in order) and written
+// to the slot of mode (l, 0), which is then the only slot the object-gradient kernel reads.
+// The probe row sits in shared memory for the whole batch and the object row is read once per
+// position.  Probe-gradient sums go to buffer gPs + split*gp_stride (read-modify-write).
+// grid (F/rpb, L, nsplit), block T*M*rpb <= 256, dynamic smem row_adj_l_smem<F>(M, rpb)
+// ---------------------------------------------------------------------------------------
+constexpr int kRowAdjLSmemMax = 200 * 1024;       // dynamic shared memory cap of k_row_adj_l / k_row_fwd_l
+template <int F>
+__host__ __device__ constexpr int row_adj_l_smem(int M, int rpb) {
+  return (M * rpb * F + 2 * M * rpb * Xch<F>::region_rows + 2 * rpb * F) * (int)sizeof(float2);
+}
+
+// Next position of this split after b whose index is valid, or -1 (uniform over the block).
+__device__ __forceinline__ int next_pos(const int2* spos, int b, int nb, int nsplit) {
+  for (int bb = b + nsplit; bb < nb; bb += nsplit)
+    if (spos[bb].x >= 0) return bb;
+  return -1;
+}
+
+// Copies of the rpb object rows of position (y, x) (8-byte pieces: x may be odd).
+template <int F>
+__device__ __forceinline__ void prefetch_orows(const float2* __restrict__ Ol, int Wl, int2 yx, int row0, int rpb,
+                                               float2* dst) {
+  for (int e = threadIdx.x; e < rpb * F; e += blockDim.x) {
+    const int rr = e / F, c = e % F;
+    cp_async8(dst + e, Ol + (long long)(yx.x + row0 + rr) * Wl + yx.y + c);
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(256, (F <= 256 ? 2 : 1))
+k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
+            float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = N1, RR = Xch<F>::region_rows;
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
+  const int M = a.M, V = M * rpb;
+  float2* Psm = smem;                                 // [V][F]    probe rows
+  float2* Sst = Psm + V * F;                          // [2][V][RR] scratch rows; the current buffer
+                                                      //   is also the FFT exchange and the mode-sum area
+  float2* Ost = Sst + 2 * V * RR;                     // [2][rpb][F] object rows
+  const int vec = threadIdx.x / T, t = threadIdx.x % T;
+  const int rr = vec / M, m = vec % M;
+  const int row0 = blockIdx.x * rpb, r = row0 + rr;
+  const int l = blockIdx.y, split = blockIdx.z;
+  const int cm = l * M + m - a.chunk_base;
+  const int slot0 = l * M - a.chunk_base;             // slot of the mode sum
+  stage_batch(a, l, spos, ssig);
+  {
+    const float2* Prow = P + ((long long)(l * M + m) * F + r) * F;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) Psm[vec * F + t + N1 * n2] = __ldg(Prow + t + N1 * n2);
+  }
+  const float2* Ol = O + a.obj_off[l];
+  const int Wl = a.obj_w[l];
+  // position b's scratch row of this vector (2 KB contiguous, 16-byte pieces by its T threads)
+  // and the block's object rows, into buffer buf
+  auto prefetch = [&](int b, int buf) {
+    const float2* row = S + (((long long)b * a.C + cm) * F + r) * F;
+    float2* dst = Sst + (buf * V + vec) * RR;
+#pragma unroll
+    for (int k = 0; k < F / (2 * T); ++k) cp_async16(dst + 2 * (t + T * k), row + 2 * (t + T * k));
+    prefetch_orows<F>(Ol, Wl, spos[b], row0, rpb, Ost + buf * rpb * F);
+    cp_async_commit();
+  };
+  float2 acc[N2];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) acc[n2] = make_float2(0.f, 0.f);
+  int b = next_pos(spos, split - nsplit, a.nb, nsplit);
+  if (b >= 0) prefetch(b, 0);
+  for (int buf = 0; b >= 0; buf ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();                                  // position b has landed; buffer buf^1 is free
+    const int bn = next_pos(spos, b, a.nb, nsplit);
+    if (bn >= 0) prefetch(bn, buf ^ 1);
+    const float s = ssig[b];
+    float2* reg = Sst + (buf * V + vec) * RR;         // this vector's row, then its exchange/mode-sum area
+    const float2* orow = Ost + (buf * rpb + rr) * F;
+    float2 v[N2];
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) v[sl] = reg[idxO<F>(t, sl)];
+    __syncwarp();                                     // the row is in registers before the exchange reuses it
+    fft_inv_O2I<F>(v, t, reg, a.tw, WarpSync{});
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      const int c = t + N1 * n2;
+      const float2 gp = cconjmul(orow[c], v[n2]);                       // conj(p) chi
+      acc[n2].x = fmaf(s, gp.x, acc[n2].x);
+      acc[n2].y = fmaf(s, gp.y, acc[n2].y);
+      reg[c] = cscale(cconjmul(Psm[vec * F + c], v[n2]), s);            // conj(sigma P) chi
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rpb * F; e += blockDim.x) {           // modes added in order
+      const int rr2 = e / F, c = e % F;
+      const float2* red = Sst + (buf * V + rr2 * M) * RR + c;
+      float2 sum = red[0];
+      for (int mm = 1; mm < M; ++mm) sum = cadd(sum, red[mm * RR]);
+      S[(((long long)b * a.C + slot0) * F + row0 + rr2) * F + c] = sum;
+    }
+    b = bn;
+  }
+  float2* g = gPs + (long long)split * gp_stride + ((long long)(l * M + m) * F + r) * F;
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) {
+    const int c = t + N1 * n2;
+    g[c] = cadd(g[c], acc[n2]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// forward row pass over all modes of one wavelength (one mode chunk holds every mode).
+// Vector v = rr*M + m takes row r = blockIdx.x*rpb + rr of probe mode (l, m); its probe row
+// stays in registers while the block runs over the positions of its split; the object rows
+// of the next position are copied into shared memory (cp.async) during the current one.
+// grid (F/rpb, L, nsplit), block T*M*rpb <= 256, dynamic smem row_fwd_l_smem<F>(M, rpb)
+// ---------------------------------------------------------------------------------------
+template <int F>
+__host__ __device__ constexpr int row_fwd_l_smem(int M, int rpb) {
+  return (M * rpb * Xch<F>::region_rows + 2 * rpb * F) * (int)sizeof(float2);
+}
+
+template <int F>
+__global__ void __launch_bounds__(256, (F <= 256 ? 2 : 1))
+k_row_fwd_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a, int rpb,
+            int nsplit) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = N1, RR = Xch<F>::region_rows;
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
+  const int M = a.M, V = M * rpb;
+  float2* xch = smem;                                 // [V][RR]
+  float2* Ost = xch + V * RR;                         // [2][rpb][F]
+  const int vec = threadIdx.x / T, t = threadIdx.x % T;
+  const int rr = vec / M, m = vec % M;
+  const int row0 = blockIdx.x * rpb, r = row0 + rr;
+  const int l = blockIdx.y, split = blockIdx.z;
+  const int cm = l * M + m - a.chunk_base;
+  stage_batch(a, l, spos, ssig);
+  float2 pr[N2];
+  {
+    const float2* Prow = P + ((long long)(l * M + m) * F + r) * F;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) pr[n2] = __ldg(Prow + t + N1 * n2);
+  }
+  const float2* Ol = O + a.obj_off[l];
+  const int Wl = a.obj_w[l];
+  int b = next_pos(spos, split - nsplit, a.nb, nsplit);
+  if (b >= 0) {
+    prefetch_orows<F>(Ol, Wl, spos[b], row0, rpb, Ost);
+    cp_async_commit();
+  }
+  for (int buf = 0; b >= 0; buf ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();                                  // position b's rows have landed; buf^1 is free
+    const int bn = next_pos(spos, b, a.nb, nsplit);
+    if (bn >= 0) {
+      prefetch_orows<F>(Ol, Wl, spos[bn], row0, rpb, Ost + (buf ^ 1) * rpb * F);
+      cp_async_commit();
+    }
+    const float s = ssig[b];
+    const float2* orow = Ost + (buf * rpb + rr) * F;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = cmul(pr[n2], cscale(orow[t + N1 * n2], s));
+    fft_fwd_I2O<F>(v, t, xch + vec * RR, a.tw, WarpSync{});
+    float2* out = S + (((long long)b * a.C + cm) * F + r) * F;
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) out[idxO<F>(t, sl)] = v[sl];
+    b = bn;
+  }
+}
+
+// Fixed-order sum of the per-split probe-gradient buffers: out[i] = sum_s part[s][i].
+__global__ void k_sum_splits(const float2* __restrict__ part, int nsplit, long long n, float2* __restrict__ out);
+
+// ---------------------------------------------------------------------------------------
+// object gradient from one mode-summed slot per (position, wavelength) (after k_row_adj_l):
+// one block per 32x32 tile of grad O_l inside the batch's bounding box.  The positions whose
+// patches overlap the tile are listed first (ascending), then added four at a time with
+// their loads issued together.   grid (tiles of the largest box, L)
+// ---------------------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(256)
+k_obj_grad_l(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
+  __shared__ int list[kMaxB];
+  __shared__ int nlist;
+  const int l = blockIdx.y;
+  const int by0 = a.box[l][0], bx0 = a.box[l][1];
+  const int ntx = (a.box[l][3] - bx0 + kTile - 1) / kTile;
+  const int nty = (a.box[l][2] - by0 + kTile - 1) / kTile;
+  if ((int)blockIdx.x >= ntx * nty) return;          // uniform over the block
+  stage_batch(a, l, spos, ssig);
+  const int oy0 = by0 + ((int)blockIdx.x / ntx) * kTile, ox0 = bx0 + ((int)blockIdx.x % ntx) * kTile;
+  if (threadIdx.x < 32) {                             // ordered compaction by warp 0
+    int n = 0;
+    for (int b0 = 0; b0 < a.nb; b0 += 32) {
+      const int b = b0 + (int)threadIdx.x;
+      bool hit = false;
+      if (b < a.nb) {
+        const int y = spos[b].x, x = spos[b].y;
+        hit = !(y < 0 || y >= oy0 + kTile || y + F <= oy0 || x >= ox0 + kTile || x + F <= ox0);
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      if (hit) list[n + __popc(mask & ((1u << threadIdx.x) - 1u))] = b;
+      n += __popc(mask);
+    }
+    if (threadIdx.x == 0) nlist = n;
+  }
+  __syncthreads();
+  const int n = nlist;
+  const int H = a.obj_h[l], Wd = a.obj_w[l];
+  const int tx = threadIdx.x % kTile, ty0 = threadIdx.x / kTile;   // 8 row slots
+  const int ox = ox0 + tx;
+  const int slot0 = l * a.M - a.chunk_base;
+  float2 acc[kTile / 8];
+#pragma unroll
+  for (int k = 0; k < kTile / 8; ++k) acc[k] = make_float2(0.f, 0.f);
+  constexpr int PG = 4;                               // patches per group of loads
+  for (int i0 = 0; i0 < n; i0 += PG) {
+    float2 v[PG][kTile / 8];
+#pragma unroll
+    for (int pp = 0; pp < PG; ++pp) {
+      const int b = i0 + pp < n ? list[i0 + pp] : -1;
+      const int y = b >= 0 ? spos[b].x : 0, x = b >= 0 ? spos[b].y : 0;
+      const bool in_x = b >= 0 && ox >= x && ox < x + F;
+      const float2* src = S + ((long long)(b >= 0 ? b : 0) * a.C + slot0) * F * F + (ox - x);
+#pragma unroll
+      for (int k = 0; k < kTile / 8; ++k) {
+        const int oy = oy0 + ty0 + 8 * k;
+        const bool ok = in_x && oy >= y && oy < y + F;
+        v[pp][k] = ok ? src[(long long)(oy - y) * F] : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int pp = 0; pp < PG; ++pp)
+#pragma unroll
+      for (int k = 0; k < kTile / 8; ++k) acc[k] = cadd(acc[k], v[pp][k]);
   }
   float2* g = gO + a.obj_off[l];
 #pragma unroll

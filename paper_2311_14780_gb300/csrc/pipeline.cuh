@@ -16,6 +16,13 @@ namespace ptycho {
     prof_end((p), pty_ev, (st));                                     \
   } while (0)
 
+// Whether launch_pdl asks for programmatic stream serialisation (per host thread; each
+// compute call sets it from its plan's flags).
+inline bool& pdl_enabled() {
+  static thread_local bool on = true;
+  return on;
+}
+
 // Launch with programmatic stream serialisation (see pdl_wait in kernels.cuh).
 template <typename... KP, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
@@ -28,8 +35,38 @@ cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
+}
+
+template <int F, int WN>
+cudaError_t set_cols_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_col_fwd_s<F, true, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ColSCfg<F, WN>::smem_fwd);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_col_fwd_s<F, false, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColSCfg<F, WN>::smem_fwd);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_col_adj_s<F, true, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColSCfg<F, WN>::smem_adj);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_col_adj_s<F, false, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColSCfg<F, WN>::smem_adj);
+  return e;
+}
+
+// Staged column passes with WN columns per block (0 = the frame size's default).
+template <int F, int WN>
+int launch_cols_s(ptycho_plan& p, bool fwd, bool store, cudaStream_t cs, float2* S, float* Ip, const KArgs& a,
+                  const AdjArgs& aa) {
+  using Cfg = ColSCfg<F, WN>;
+  const dim3 grid(F / Cfg::W, a.nb), blk(Cfg::threads);
+  if (fwd && store)
+    PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_s<F, true, WN>, grid, blk, Cfg::smem_fwd, cs, S, Ip, a));
+  else if (fwd)
+    PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_s<F, false, WN>, grid, blk, Cfg::smem_fwd, cs, S, Ip, a));
+  else if (store)
+    PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_s<F, true, WN>, grid, blk, Cfg::smem_adj, cs, S, a, aa));
+  else
+    PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_s<F, false, WN>, grid, blk, Cfg::smem_adj, cs, S, a, aa));
+  return PTYCHO_OK;
 }
 
 template <int F>
@@ -49,6 +86,10 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_fwd);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_fwd_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  if (e == cudaSuccess) e = set_cols_smem<F, 0>();
+  if (e == cudaSuccess) e = set_cols_smem<F, 4>();
   if (e != cudaSuccess) return PTYCHO_ECUDA;
   done = 1;
   return PTYCHO_OK;
@@ -58,6 +99,7 @@ template <int F>
 int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   int rc = prepare_kernels<F>();
   if (rc) return rc;
+  pdl_enabled() = !(p.flags & PTYCHO_FLAG_NO_PDL);
   constexpr int FF = F * F;
   const bool grad = c.kind == CallKind::Adjoint;
   const bool need_loss = c.kind != CallKind::Forward;
@@ -66,6 +108,14 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const bool store = grad && p.store && !(p.flags & PTYCHO_FLAG_RECOMPUTE_COLUMNS);
   const bool rerun_rows = !p.store;     // modes in chunks: the row pass is rerun as well
   const bool obj_atomic = (p.flags & PTYCHO_FLAG_OBJ_GRAD_ATOMIC) != 0;
+  // all modes of a wavelength per adjoint row block; with several position splits the probe
+  // gradient is summed per split and the splits are added in order at the end
+  const bool adj_l = p.adj_l && !obj_atomic && p.nchunks == 1;
+  const bool col_staged = p.col_staged && p.nchunks == 1;
+  const bool fwd_l = p.fwd_l && p.nchunks == 1;
+  const bool narrow = (p.flags & PTYCHO_FLAG_NARROW_COLUMNS) != 0;
+  const int nsplit = adj_l ? p.nsplit_adj : 1;
+  float2* gPs = nsplit > 1 ? p.d_gPs : c.gP;
 
   KArgs a{};
   a.L = p.L; a.M = p.M; a.F = F; a.J = p.J;
@@ -95,6 +145,9 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.sig_part = grad && c.g_sigma ? p.d_sig_part : nullptr;
   la.I_pred = c.kind == CallKind::Forward ? c.I_pred : nullptr;
   la.remap = p.remap;
+  // the column pass adds its mode-group slices into slice 0 when every mode is in one chunk
+  const bool sum_slices = p.nchunks == 1 && p.G > 1;
+  la.Gsum = sum_slices ? 1 : p.G;
 
   AdjArgs aa{};
   aa.D = p.d_D;
@@ -107,9 +160,11 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const bool identity = c.bidx == p.d_ident && p.pos_host.size() >= (size_t)p.L * p.J * 2;
 
   p.last_launches = 0;
+  if (sum_slices && cudaMemsetAsync(p.d_cnt, 0, sizeof(int) * (size_t)p.nsets * p.B * F, st) != cudaSuccess)
+    return PTYCHO_ECUDA;
   if (grad) {
     if (cudaMemsetAsync(c.gO, 0, sizeof(float2) * p.O_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
-    if (cudaMemsetAsync(c.gP, 0, sizeof(float2) * p.P_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
+    if (cudaMemsetAsync(gPs, 0, sizeof(float2) * p.P_numel * nsplit, st) != cudaSuccess) return PTYCHO_ECUDA;
     if (c.g_bg && cudaMemsetAsync(p.d_gbg_set, 0, sizeof(float) * p.nsets * FF, st) != cudaSuccess)
       return PTYCHO_ECUDA;
   }
@@ -132,6 +187,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     cudaStream_t cs = streams[set];
     float2* S = p.d_S + set * set_S;
     float* Ip = p.d_Ipart + set * set_I;
+    int* cnt = sum_slices ? p.d_cnt + (long long)set * p.B * (F / ColCfg<F>::W) : nullptr;
     la.Ipart = Ip;
     la.D = grad ? p.d_D + set * set_F : nullptr;
     aa.D = p.d_D + set * set_F;
@@ -160,25 +216,33 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
-      PTY_LAUNCH(p, kRowFwd, cs,
-                 launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
+      if (fwd_l)
+        PTY_LAUNCH(p, kRowFwd, cs,
+                   launch_pdl(k_row_fwd_l<F>, dim3(F / p.rpb_adj, p.L, p.nsplit_fwd), FftShape<F>::N1 * p.M * p.rpb_adj,
+                              row_fwd_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, a, p.rpb_adj, p.nsplit_fwd));
+      else
+        PTY_LAUNCH(p, kRowFwd, cs,
+                   launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
       const dim3 col_grid(F / ColCfg<F>::W, p.G, a.nb);
-      if (p.has_tma && store)
+      if (col_staged) {
+        rc = narrow ? launch_cols_s<F, 4>(p, true, store, cs, S, Ip, a, aa) : launch_cols_s<F, 0>(p, true, store, cs, S, Ip, a, aa);
+        if (rc) return rc;
+      } else if (p.has_tma && store)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
-                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
+                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0), cnt));
       else if (p.has_tma)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, false>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
-                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
+                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0), cnt));
       else if (store)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, true>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
-                                              (int)(ch == 0)));
+                                              (int)(ch == 0), cnt));
       else
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, false>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
-                                              (int)(ch == 0)));
+                                              (int)(ch == 0), cnt));
     }
-    PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(FF / kLossThreads, a.nb), kLossThreads, 0, cs, a, la));
+    PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(loss_blocks<F>(), a.nb), kLossThreads, 0, cs, a, la));
     if (!grad) continue;
-    if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_remap_adj<F>, dim3(FF / 256, a.nb), 256, 0, cs, a, aa));
+    if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_remap_adj<F>, dim3(FF / 256, (a.nb + kRtPos - 1) / kRtPos), 256, 0, cs, a, aa));
     if (c.g_bg)                                       // per-set background-gradient sum, batch order
       PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_bg_accum<F>, dim3(FF / 256), 256, 0, cs,
                                               (const float*)(p.remap ? aa.Gt : aa.D), a.nb, p.d_gbg_set + set * FF));
@@ -189,7 +253,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       if (!store && rerun_rows)
         PTY_LAUNCH(p, kRowFwd, cs,
                    launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
-      if (p.has_tma && store)
+      if (col_staged) {
+        rc = narrow ? launch_cols_s<F, 4>(p, false, store, cs, S, Ip, a, aa) : launch_cols_s<F, 0>(p, false, store, cs, S, Ip, a, aa);
+        if (rc) return rc;
+      } else if (p.has_tma && store)
         PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_adj, cs,
                                               p.tmap_S[set], S, a, aa));
       else if (p.has_tma)
@@ -202,6 +269,19 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       // the probe and object gradients accumulate in batch order across the streams
       if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_radj[(k - 1) % nsets], 0) != cudaSuccess)
         return PTYCHO_ECUDA;
+      if (adj_l) {
+        constexpr int T = FftShape<F>::N1;
+        PTY_LAUNCH(p, kRowAdj, cs,
+                   launch_pdl(k_row_adj_l<F>, dim3(F / p.rpb_adj, p.L, nsplit), T * p.M * p.rpb_adj,
+                              row_adj_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, gPs, (long long)p.P_numel, a,
+                              p.rpb_adj, nsplit));
+        if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+        if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_og[(k - 1) % nsets], 0) != cudaSuccess)
+          return PTYCHO_ECUDA;
+        PTY_LAUNCH(p, kObjGrad, cs, launch_pdl(k_obj_grad_l<F>, dim3(max_tiles, p.L), 256, 0, cs, S, c.gO, a));
+        if (nsets > 1 && cudaEventRecord(p.ev_og[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+        continue;
+      }
       if (obj_atomic)
         PTY_LAUNCH(p, kRowAdj, cs,
                    launch_pdl(k_row_adj<F, true>, dim3(F / RowAdjCfg<F>::RPB, a.chunk_len), RowAdjCfg<F>::threads, RowAdjCfg<F>::smem, cs, c.O, c.P, S, c.gP, c.gO, a));
@@ -221,10 +301,13 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
         cudaStreamWaitEvent(st, p.ev_join[i - 1], 0) != cudaSuccess)
       return PTYCHO_ECUDA;
   }
+  if (grad && nsplit > 1)
+    PTY_LAUNCH(p, kRowAdj, st,
+               launch_pdl(k_sum_splits, dim3(4 * p.sms), 256, 0, st, (const float2*)gPs, nsplit, p.P_numel, c.gP));
   if (grad && c.g_sigma)
     PTY_LAUNCH(p, kLossReduce, st,
                launch_pdl(k_sigma_grad, dim3((p.J + 255) / 256), 256, 0, st, (const int32_t*)c.bidx, c.nbatch, p.J,
-                          (const double*)p.d_sig_part, FF / kLossThreads, c.sigma, c.g_sigma));
+                          (const double*)p.d_sig_part, loss_blocks<F>(), c.sigma, c.g_sigma));
   if (grad && c.g_bg)
     PTY_LAUNCH(p, kLossReduce, st,
                launch_pdl(k_sum_sets, dim3(FF / 256), 256, 0, st, (const float*)p.d_gbg_set, nsets, (long long)FF,
@@ -233,7 +316,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     double* out = c.loss;
     if (out) {
       PTY_LAUNCH(p, kLossReduce, st,
-                 launch_pdl(k_loss_reduce, 1, 256, 0, st, p.d_loss_part, (long long)c.nbatch * (FF / kLossThreads), out));
+                 launch_pdl(k_loss_reduce, 1, 256, 0, st, p.d_loss_part, (long long)c.nbatch * loss_blocks<F>(), out));
     }
   }
   return PTYCHO_OK;

@@ -166,6 +166,7 @@ int plain_adjoint(ptycho_plan& p, const CallArgs& c, float2* psi, float* Ibuf, f
   la.D = Dbuf;                                        // [Bp][F][F], sized by the caller
   la.loss_part = p.d_loss_part;
   la.remap = p.remap;
+  la.Gsum = 1;
   AdjArgs aa{};
   aa.D = Dbuf;
   aa.rt_ptr = p.d_rt_ptr;
@@ -185,8 +186,8 @@ int plain_adjoint(ptycho_plan& p, const CallArgs& c, float2* psi, float* Ibuf, f
     PTY_LAUNCH(p, kRowFwd, st, k_pl_rows<F, false><<<dim3(F / RowCfg<F>::RPB, frames), RowCfg<F>::threads, RowCfg<F>::smem, st>>>(psi, p.d_tw));
     PTY_LAUNCH(p, kColFwd, st, k_pl_cols<F, false><<<dim3(F / ColCfg<F>::W, frames), ColCfg<F>::threads, ColCfg<F>::smem_xch, st>>>(psi, p.d_tw, inv));
     PTY_LAUNCH(p, kColFwd, st, k_pl_intensity<F><<<dim3(FF / 256, a.nb), 256, 0, st>>>(psi, Ibuf, LM));
-    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<dim3(FF / kLossThreads, a.nb), kLossThreads, 0, st>>>(a, la));
-    if (p.remap) PTY_LAUNCH(p, kRemapAdj, st, k_remap_adj<F><<<dim3(FF / 256, a.nb), 256, 0, st>>>(a, aa));
+    PTY_LAUNCH(p, kLoss, st, k_loss<F><<<dim3(loss_blocks<F>(), a.nb), kLossThreads, 0, st>>>(a, la));
+    if (p.remap) PTY_LAUNCH(p, kRemapAdj, st, k_remap_adj<F><<<dim3(FF / 256, (a.nb + kRtPos - 1) / kRtPos), 256, 0, st>>>(a, aa));
     PTY_LAUNCH(p, kColAdj, st, k_pl_mul<F><<<dim3(FF / 256, LM, a.nb), 256, 0, st>>>(psi, p.remap ? Gbuf : Dbuf, LM));
     PTY_LAUNCH(p, kColAdj, st, k_pl_cols<F, true><<<dim3(F / ColCfg<F>::W, frames), ColCfg<F>::threads, ColCfg<F>::smem_xch, st>>>(psi, p.d_tw, inv));
     PTY_LAUNCH(p, kRowAdj, st, k_pl_rows<F, true><<<dim3(F / RowCfg<F>::RPB, frames), RowCfg<F>::threads, RowCfg<F>::smem, st>>>(psi, p.d_tw));
@@ -194,7 +195,7 @@ int plain_adjoint(ptycho_plan& p, const CallArgs& c, float2* psi, float* Ibuf, f
   }
   if (c.loss) {
     PTY_LAUNCH(p, kLossReduce, st,
-               k_loss_reduce<<<1, 256, 0, st>>>(p.d_loss_part, (long long)c.nbatch * (FF / kLossThreads), c.loss));
+               k_loss_reduce<<<1, 256, 0, st>>>(p.d_loss_part, (long long)c.nbatch * loss_blocks<F>(), c.loss));
   }
   return PTYCHO_OK;
 }

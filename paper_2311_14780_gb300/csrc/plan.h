@@ -24,6 +24,14 @@ struct ptycho_plan {
   // batching: B positions per batch, modes split into chunks of C, columns kernels use
   // G groups of MG modes; store = 1 keeps Psi in S between the forward and the adjoint.
   int store = 1, B = 1, C = 1, nchunks = 1, G = 1, MG = 1;
+  // adjoint row pass over all modes of a wavelength per block (k_row_adj_l): rows per block,
+  // position splits (each with its own probe-gradient buffer when nsplit > 1)
+  int adj_l = 0, rpb_adj = 1, nsplit_adj = 1;
+  // forward row pass over all modes of a wavelength per block (k_row_fwd_l), same rows per block
+  int fwd_l = 0, nsplit_fwd = 1;
+  // staged column passes (k_col_fwd_s / k_col_adj_s): one block per W columns of a position
+  // runs over all its modes, so the column passes leave a single intensity slice (G = 1)
+  int col_staged = 0;
   long long scratch_budget = 0;
 
   // nsets buffer sets let consecutive position batches overlap: batch k runs on stream
@@ -48,15 +56,17 @@ struct ptycho_plan {
   float* d_rt_w = nullptr;
   float2* d_S = nullptr;                       // [nsets][B][C][F][F]
   float* d_Ipart = nullptr;                    // [nsets][B][G][F][F]
+  int* d_cnt = nullptr;                        // [nsets][B][F/W] group-slice counters (zero between launches)
   float* d_D = nullptr;                        // [nsets][B][F][F]
   float* d_Gt = nullptr;                       // [nsets][B][F][F] R^T D (remap only)
   double* d_loss_part = nullptr;
-  double* d_sig_part = nullptr;                // [J][F*F/256] sigma-gradient partials
+  double* d_sig_part = nullptr;                // [J][loss_blocks] sigma-gradient partials
   float* d_gbg_set = nullptr;                  // [nsets][F][F] background-gradient accumulators
   float* d_gsig = nullptr;                     // [J] sigma gradient (ptycho_step)
   float* d_gbg = nullptr;                      // [F][F] background gradient (ptycho_step)
   float2* d_gO = nullptr;
   float2* d_gP = nullptr;
+  float2* d_gPs = nullptr;                     // [nsplit_adj][L][M][F][F] probe-gradient partials
   int* d_status = nullptr;                     // device status word, see ptycho_plan_status
 
   // TMA tensor maps of each scratch set, viewed as [B*C*F rows][F columns] of 8-byte elements

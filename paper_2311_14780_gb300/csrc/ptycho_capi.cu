@@ -48,6 +48,17 @@ k_sigma_grad(const int32_t* __restrict__ bidx, int nbatch, int J, const double* 
   g[j] = sj != 0.f ? (float)(2.0 * s / (double)sj) : 0.f;
 }
 
+// out[i] = sum over the probe-gradient splits, in split order, of part[s][i].
+__global__ void __launch_bounds__(256)
+k_sum_splits(const float2* __restrict__ part, int nsplit, long long n, float2* __restrict__ out) {
+  pdl_wait();
+  for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    float2 s = part[i];
+    for (int k = 1; k < nsplit; ++k) s = cadd(s, part[(long long)k * n + i]);
+    out[i] = s;
+  }
+}
+
 // out[u] = sum over the scratch sets, in set order, of acc[set][u].
 __global__ void __launch_bounds__(256)
 k_sum_sets(const float* __restrict__ acc, int nsets, long long n, float* __restrict__ out) {
@@ -125,7 +136,7 @@ namespace {
 constexpr long long kMaxScratch = 2ll << 30;   // default upper bound of the FFT scratch
 constexpr long long kBatchEvals = 128;         // evaluations per batch the default aims for
 constexpr long long kBatchRows = 32768;        // and at least this many 1D FFT rows per pass
-constexpr int kDefaultOverlap = 2;             // position batches in flight
+constexpr int kDefaultOverlap = 3;             // position batches in flight
 constexpr double kPi = 3.14159265358979323846;
 
 bool supported_F(int F) { return F == 64 || F == 128 || F == 256 || F == 512; }
@@ -163,7 +174,7 @@ void free_plan(ptycho_plan* p) {
   }
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
-                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg};
+                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs, p->d_cnt};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -334,7 +345,8 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   p->L = g->L; p->M = g->M; p->F = F; p->J = g->J;
   p->remap = g->remap ? 1 : 0;
   p->loss_kind = g->loss;
-  p->flags = g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_OBJ_GRAD_ATOMIC);
+  p->flags = g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_OBJ_GRAD_ATOMIC | PTYCHO_FLAG_NARROW_COLUMNS |
+                         PTYCHO_FLAG_NO_PDL);
   // measured: recomputing the column DFT beats keeping Psi from F = 256 up
   if (!(g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_KEEP_PSI)) && g->F >= 256)
     p->flags |= PTYCHO_FLAG_RECOMPUTE_COLUMNS;
@@ -388,6 +400,50 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   G = std::max<long long>(1, std::min<long long>(G, p->C));
   p->MG = (int)((p->C + G - 1) / G);
   p->G = (p->C + p->MG - 1) / p->MG;
+  if (p->store && (g->flags & PTYCHO_FLAG_STAGED_COLUMNS) && g->col_groups <= 0) {
+    p->col_staged = 1;
+    p->G = 1;
+    p->MG = p->C;
+  }
+
+  // adjoint row pass over all modes of a wavelength per block (see PTYCHO_FLAG_UNFUSED_ROW_ADJ)
+  {
+    int T = 0, smem = 0;
+    switch (F) {
+      case 64: T = ptycho::FftShape<64>::N1; break;
+      case 128: T = ptycho::FftShape<128>::N1; break;
+      case 256: T = ptycho::FftShape<256>::N1; break;
+      default: T = ptycho::FftShape<512>::N1; break;
+    }
+    // measured: at F = 512 the fused kernel's registers (two 32-value rows per thread) cost
+    // more occupancy than the probe reuse saves, so F = 512 keeps one block per mode
+    if (p->store && !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) && T * g->M <= 256 && F <= 256) {
+      int rpb = 1;
+      while (2 * rpb * T * g->M <= 128 && 2 * rpb <= F) rpb *= 2;
+      switch (F) {
+        case 64: smem = ptycho::row_adj_l_smem<64>(g->M, rpb); break;
+        case 128: smem = ptycho::row_adj_l_smem<128>(g->M, rpb); break;
+        case 256: smem = ptycho::row_adj_l_smem<256>(g->M, rpb); break;
+        default: smem = ptycho::row_adj_l_smem<512>(g->M, rpb); break;
+      }
+      if (smem <= ptycho::kRowAdjLSmemMax) {
+        p->adj_l = 1;
+        p->rpb_adj = rpb;
+        // enough blocks for three per SM: split the batch's positions, each split summing its
+        // probe gradient into a buffer of its own (bounded to 512 MB in all)
+        const long long base = (long long)(F / rpb) * g->L;
+        long long ns = (3ll * p->sms + base - 1) / base;
+        ns = std::min<long long>(ns, std::min<long long>(64, p->B));
+        while (ns > 1 && ns * p->P_numel * (long long)sizeof(float2) > (512ll << 20)) --ns;
+        p->nsplit_adj = (int)std::max<long long>(1, ns);
+        // the forward row pass: same blocks, positions split for four blocks per SM
+        if (g->flags & PTYCHO_FLAG_FUSED_ROW_FWD) {
+          p->fwd_l = 1;
+          p->nsplit_fwd = (int)std::max<long long>(1, std::min<long long>((4ll * p->sms + base - 1) / base, p->B));
+        }
+      }
+    }
+  }
 
   int rc = PTYCHO_OK;
   const long long FF = (long long)F * F;
@@ -412,14 +468,17 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   }
   rc = rc ? rc : dalloc(p, &p->d_S, (long long)p->nsets * p->B * p->C * FF);
   rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->nsets * p->B * p->G * FF);
+  rc = rc ? rc : dalloc(p, &p->d_cnt, (long long)p->nsets * p->B * F);   // >= F/W counters per position
+  if (!rc && cudaMemset(p->d_cnt, 0, sizeof(int) * (size_t)p->nsets * p->B * F) != cudaSuccess) rc = PTYCHO_ECUDA;
   rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->nsets * p->B * FF);
-  rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / ptycho::kLossThreads));
-  rc = rc ? rc : dalloc(p, &p->d_sig_part, (long long)g->J * (FF / ptycho::kLossThreads));
+  rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
+  rc = rc ? rc : dalloc(p, &p->d_sig_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
   rc = rc ? rc : dalloc(p, &p->d_gbg_set, (long long)p->nsets * FF);
   rc = rc ? rc : dalloc(p, &p->d_gsig, g->J);
   rc = rc ? rc : dalloc(p, &p->d_gbg, FF);
   rc = rc ? rc : dalloc(p, &p->d_gO, p->O_numel);
   rc = rc ? rc : dalloc(p, &p->d_gP, p->P_numel);
+  if (p->nsplit_adj > 1) rc = rc ? rc : dalloc(p, &p->d_gPs, (long long)p->nsplit_adj * p->P_numel);
   rc = rc ? rc : dalloc(p, &p->d_status, 1);
   if (!rc && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = PTYCHO_ECUDA;
   if (rc) { free_plan(p); return rc; }

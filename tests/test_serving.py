@@ -143,11 +143,14 @@ def test_plain_step_matches_fused_step(F):
     s1, s2 = AdamState(plan, 1e-2, 1e-2), AdamState(plan, 1e-2, 1e-2)
     l1 = torch.zeros(1, dtype=torch.float64, device=dev)
     l2 = torch.zeros(1, dtype=torch.float64, device=dev)
-    for _ in range(3):
+    for it in range(3):
         plan.step(s1, O1, P1, r.I_meas, loss_out=l1)
         plan.plain_step(s2, O2, P2, r.I_meas, loss_out=l2)
         torch.cuda.synchronize()
-        assert abs(float(l1.item()) - float(l2.item())) <= REL * abs(float(l1.item()))
+        # the first loss is taken at identical parameters; later ones after Adam steps that
+        # differ on near-zero gradient components (see below), which moves the loss by ~1e-5
+        bar = REL if it == 0 else 10 * REL
+        assert abs(float(l1.item()) - float(l2.item())) <= bar * abs(float(l1.item())), it
     # parameters: Adam's early steps are +-lr per component whatever the gradient size, so
     # components whose gradient is at the level of FP32 rounding (object pixels under the
     # probe's far tails) take the sign of that rounding, which the plain form's atomic
