@@ -141,38 +141,13 @@ k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   }
 }
 
-// After the G mode-group blocks of (position b, column block) have written their intensity
-// slices, the last of them to finish (a counter per (b, column block), reset for the next
-// launch) adds the G slices in group order into slice 0, so that later passes read one slice.
-// The order of the sum does not depend on which block comes last.
-template <int F, int W>
-__device__ __forceinline__ void sum_group_slices(float* __restrict__ Ipart, int* __restrict__ cnt, int G, int b,
-                                                 int col0) {
-  __shared__ int s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(cnt + b * (F / W) + col0 / W, 1) == G - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int cc0 = (col0 + F / 2) & (F - 1);           // the block's W centred columns are contiguous
-  float* base = Ipart + (long long)b * G * F * F + cc0;
-  for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
-    const int row = e / W, c = e % W;
-    float sum = __ldcg(base + row * F + c);
-    for (int g = 1; g < G; ++g) sum += __ldcg(base + (long long)g * F * F + row * F + c);
-    base[row * F + c] = sum;
-  }
-  if (threadIdx.x == 0) cnt[b * (F / W) + col0 / W] = 0;
-}
-
 // ---------------------------------------------------------------------------------------
 // forward column pass: column DFT (second half of f4), |Psi|^2 summed over a mode group
 // grid (F/W, G, nb)
 // ---------------------------------------------------------------------------------------
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
-k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk, int* __restrict__ cnt) {
+k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk) {
   pdl_wait();
   pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
@@ -206,7 +181,6 @@ k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_
     if (!first_chunk) val += dst[rc * F + cc];
     dst[rc * F + cc] = val;
   }
-  if (cnt && a.G > 1) sum_group_slices<F, W>(Ipart, cnt, a.G, b, blockIdx.x * W);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -245,7 +219,7 @@ __device__ __forceinline__ void col_tma_issue(float2* stage, const CUtensorMap* 
 template <int F, bool STORE>
 __global__ void __launch_bounds__(ColCfg<F>::threads)
 k_col_fwd_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, float* __restrict__ Ipart, KArgs a,
-              int first_chunk, int* __restrict__ cnt) {
+              int first_chunk) {
   pdl_wait();
   pdl_trigger();
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
@@ -300,7 +274,6 @@ k_col_fwd_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, f
     if (!first_chunk) val += dst[rc * F + cc];
     dst[rc * F + cc] = val;
   }
-  if (cnt && a.G > 1) sum_group_slices<F, W>(Ipart, cnt, a.G, b, blockIdx.x * W);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -403,7 +376,7 @@ struct LossArgs {
   double* sig_part;              // [nbatch][loss_blocks] sums of D * (remapped sum |Psi|^2), or null
   float* I_pred;                 // [J][F][F] or null
   int remap;
-  int Gsum;                      // intensity slices to add (1 once the column pass has summed them)
+  int Gsum;                      // intensity slices (mode groups) to add
 };
 
 __device__ __forceinline__ float model_I(const float* Ip, const float* bg, int G, int FF, int u) {

@@ -145,9 +145,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.sig_part = grad && c.g_sigma ? p.d_sig_part : nullptr;
   la.I_pred = c.kind == CallKind::Forward ? c.I_pred : nullptr;
   la.remap = p.remap;
-  // the column pass adds its mode-group slices into slice 0 when every mode is in one chunk
-  const bool sum_slices = p.nchunks == 1 && p.G > 1;
-  la.Gsum = sum_slices ? 1 : p.G;
+  la.Gsum = p.G;
 
   AdjArgs aa{};
   aa.D = p.d_D;
@@ -160,8 +158,6 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const bool identity = c.bidx == p.d_ident && p.pos_host.size() >= (size_t)p.L * p.J * 2;
 
   p.last_launches = 0;
-  if (sum_slices && cudaMemsetAsync(p.d_cnt, 0, sizeof(int) * (size_t)p.nsets * p.B * F, st) != cudaSuccess)
-    return PTYCHO_ECUDA;
   if (grad) {
     if (cudaMemsetAsync(c.gO, 0, sizeof(float2) * p.O_numel, st) != cudaSuccess) return PTYCHO_ECUDA;
     if (cudaMemsetAsync(gPs, 0, sizeof(float2) * p.P_numel * nsplit, st) != cudaSuccess) return PTYCHO_ECUDA;
@@ -187,7 +183,6 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     cudaStream_t cs = streams[set];
     float2* S = p.d_S + set * set_S;
     float* Ip = p.d_Ipart + set * set_I;
-    int* cnt = sum_slices ? p.d_cnt + (long long)set * p.B * (F / ColCfg<F>::W) : nullptr;
     la.Ipart = Ip;
     la.D = grad ? p.d_D + set * set_F : nullptr;
     aa.D = p.d_D + set * set_F;
@@ -229,16 +224,16 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
         if (rc) return rc;
       } else if (p.has_tma && store)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
-                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0), cnt));
+                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
       else if (p.has_tma)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, false>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
-                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0), cnt));
+                                              p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
       else if (store)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, true>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
-                                              (int)(ch == 0), cnt));
+                                              (int)(ch == 0)));
       else
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, false>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
-                                              (int)(ch == 0), cnt));
+                                              (int)(ch == 0)));
     }
     PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(loss_blocks<F>(), a.nb), kLossThreads, 0, cs, a, la));
     if (!grad) continue;

@@ -56,7 +56,6 @@ struct ptycho_plan {
   float* d_rt_w = nullptr;
   float2* d_S = nullptr;                       // [nsets][B][C][F][F]
   float* d_Ipart = nullptr;                    // [nsets][B][G][F][F]
-  int* d_cnt = nullptr;                        // [nsets][B][F/W] group-slice counters (zero between launches)
   float* d_D = nullptr;                        // [nsets][B][F][F]
   float* d_Gt = nullptr;                       // [nsets][B][F][F] R^T D (remap only)
   double* d_loss_part = nullptr;

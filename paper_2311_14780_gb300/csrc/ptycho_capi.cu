@@ -174,7 +174,7 @@ void free_plan(ptycho_plan* p) {
   }
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
-                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs, p->d_cnt};
+                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -468,8 +468,6 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   }
   rc = rc ? rc : dalloc(p, &p->d_S, (long long)p->nsets * p->B * p->C * FF);
   rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->nsets * p->B * p->G * FF);
-  rc = rc ? rc : dalloc(p, &p->d_cnt, (long long)p->nsets * p->B * F);   // >= F/W counters per position
-  if (!rc && cudaMemset(p->d_cnt, 0, sizeof(int) * (size_t)p->nsets * p->B * F) != cudaSuccess) rc = PTYCHO_ECUDA;
   rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->nsets * p->B * FF);
   rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
   rc = rc ? rc : dalloc(p, &p->d_sig_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
