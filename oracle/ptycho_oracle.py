@@ -20,6 +20,9 @@ Readings of points where the paper is silent (each also recorded in the design n
   wavelengths share one detector grid;
 * integer scan shift: the patch is O_l[y:y+F, x:x+F]; a patch outside the object is
   an error (no wrap-around, no clamping);
+* fractional scan offsets (optional): the integer patch is resampled at r + delta by the
+  Fourier shift theorem, taking the patch as one period of a band-limited function (so
+  the edge rows and columns wrap; the probe is negligible there);
 * tilted-plane remap: a fixed bilinear operator R from the model grid (uniform in
   sample-plane spatial frequency) to the camera grid, derived from the camera being
   perpendicular to the specular beam (Section "Experimental setup"); taps outside the
@@ -36,7 +39,10 @@ zero loss and zero gradient at noiseless truth, central finite differences, rema
 dot-product / identity / constant tests, the Adam first-step closed form and the
 paper's geometry numbers; for the sigma and background gradients: finite differences,
 the intensity-level form of the sigma gradient that Parseval's theorem gives, and the
-identity between the sigma gradient and the probe gradient along P -> cP).  The tilted-plane remap formula itself is a reading of the
+identity between the sigma gradient and the probe gradient along P -> cP; for the
+fractional offsets: whole-pixel offsets as cyclic rolls, band-limited plane waves sampled
+at the shifted points, unitarity, composition, the adjoint identity, reduction to the
+integer model, and finite differences of the loss in the offsets, O and P).  The tilted-plane remap formula itself is a reading of the
 cited geometry and is only partially pinned (identity limit, constants, adjointness,
 the paper's NA and pixel-ratio figures).
 """
@@ -66,6 +72,35 @@ def f2_shift(O_l: np.ndarray, s_j: Sequence[int], F: int) -> np.ndarray:
     if y < 0 or x < 0 or y + F > H or x + F > W:
         raise ValueError(f"patch at ({y},{x}) of size {F} leaves the {H}x{W} object")
     return O_l[y:y + F, x:x + F]
+
+
+def _shift_ramp(F: int, delta: Sequence[float]) -> np.ndarray:
+    """exp(2 pi i (f_y d_y + f_x d_x)) on the DFT grid, f = k / F in numpy's fftfreq order."""
+    fy = np.fft.fftfreq(F)[:, None]
+    fx = np.fft.fftfreq(F)[None, :]
+    return np.exp(2j * np.pi * (fy * float(delta[0]) + fx * float(delta[1])))
+
+
+def f2_subpixel(patch: np.ndarray, delta: Sequence[float]) -> np.ndarray:
+    """f2 for a fractional part of the scan position: the patch resampled at r + delta by the
+    Fourier shift theorem (the paper shifts with it, Section "Benchmarking ..."), the patch
+    taken as one period of a band-limited function.  delta = (rows, cols) in pixels."""
+    F = patch.shape[0]
+    return np.fft.ifft2(np.fft.fft2(patch) * _shift_ramp(F, delta))
+
+
+def f2_subpixel_adjoint(g: np.ndarray, delta: Sequence[float]) -> np.ndarray:
+    """Adjoint (= inverse) of f2_subpixel: the conjugate phase ramp."""
+    F = g.shape[0]
+    return np.fft.ifft2(np.fft.fft2(g) * np.conj(_shift_ramp(F, delta)))
+
+
+def f2_subpixel_derivative(patch: np.ndarray, delta: Sequence[float], axis: int) -> np.ndarray:
+    """d f2_subpixel / d delta[axis]: the shift theorem's factor 2 pi i f along that axis."""
+    F = patch.shape[0]
+    f = np.fft.fftfreq(F)
+    fac = 2j * np.pi * (f[:, None] if axis == 0 else f[None, :])
+    return np.fft.ifft2(np.fft.fft2(patch) * _shift_ramp(F, delta) * fac)
 
 
 def f3_interaction(P_scaled: np.ndarray, patch: np.ndarray) -> np.ndarray:
@@ -220,53 +255,61 @@ def _sigma(sigma, j):
     return 1.0 if sigma is None else float(sigma[j])
 
 
-def frame_fields(O, P, pos, j, sigma=None):
+def frame_patch(O_l, pos, l, j, F, delta=None):
+    """f2: the object patch of frame j at wavelength l; with delta [L][J][2] the integer
+    window is shifted further by the fractional offset delta[l][j]."""
+    p = f2_shift(O_l, pos[l][j], F)
+    return p if delta is None else f2_subpixel(p, delta[l][j])
+
+
+def frame_fields(O, P, pos, j, sigma=None, delta=None):
     """Exit waves and propagated fields Psi_{j,l,m} for one frame (f1..f4)."""
     L, M, F = P.shape[0], P.shape[1], P.shape[2]
     s = _sigma(sigma, j)
     patches, Psi = [], np.empty((L, M, F, F), np.complex128)
     for l in range(L):
-        p = f2_shift(O[l], pos[l][j], F)
+        p = frame_patch(O[l], pos, l, j, F, delta)
         patches.append(p)
         for m in range(M):
             Psi[l, m] = f4_propagate(f3_interaction(f1_power(P[l, m], s), p))
     return patches, Psi
 
 
-def predict_frame(O, P, pos, j, sigma=None, bg=None, taps=None) -> np.ndarray:
+def predict_frame(O, P, pos, j, sigma=None, bg=None, taps=None, delta=None) -> np.ndarray:
     """Eq. 1 for frame j: remap( sum_l sum_m |D[sigma_j P_lm O_l(r - s_j)]|^2 + N )."""
-    _, Psi = frame_fields(O, P, pos, j, sigma)
+    _, Psi = frame_fields(O, P, pos, j, sigma, delta)
     I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
     return f5_measure(I_sum, bg, taps)
 
 
-def predict(O, P, pos, sigma=None, bg=None, taps=None, frames=None) -> np.ndarray:
+def predict(O, P, pos, sigma=None, bg=None, taps=None, frames=None, delta=None) -> np.ndarray:
     """Predicted camera-grid patterns for the requested frames (default: all)."""
     J = pos.shape[1]
     frames = range(J) if frames is None else frames
-    return np.stack([predict_frame(O, P, pos, j, sigma, bg, taps) for j in frames])
+    return np.stack([predict_frame(O, P, pos, j, sigma, bg, taps, delta) for j in frames])
 
 
-def loss(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None) -> float:
+def loss(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None, delta=None) -> float:
     """Total loss over the requested frames and their masked pixels."""
     F = P.shape[2]
     J = pos.shape[1]
     frames = range(J) if frames is None else frames
     total = 0.0
     for j in frames:
-        Ic = predict_frame(O, P, pos, j, sigma, bg, taps)
+        Ic = predict_frame(O, P, pos, j, sigma, bg, taps, delta)
         mk = frame_mask(mask, j, F, taps)
         total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
     return total
 
 
-def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None):
+def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None, delta=None):
     """Loss and its gradient (dL/dRe + i dL/dIm) with respect to every O_l and P_lm.
 
     For each frame: forward fields Psi_{lm}; I = sum |Psi|^2 (+bg); camera pattern R I;
     D = mask * dL/dI_cam; G = R^T D; chi_{lm} = f4^-1(2 G Psi_{lm}) is the gradient
     with respect to the exit wave; then grad P_lm += conj(sigma p_l) chi_lm and
-    grad O_l[patch] += conj(sigma P_lm) chi_lm.
+    grad O_l[patch] += conj(sigma P_lm) chi_lm (with sub-pixel offsets, the patch
+    gradient goes through the adjoint of the Fourier shift before it is added).
     """
     L, M, F = P.shape[0], P.shape[1], P.shape[2]
     J = pos.shape[1]
@@ -276,7 +319,7 @@ def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=N
     total = 0.0
     for j in frames:
         s = _sigma(sigma, j)
-        patches, Psi = frame_fields(O, P, pos, j, sigma)
+        patches, Psi = frame_fields(O, P, pos, j, sigma, delta)
         I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
         Ic = f5_measure(I_sum, bg, taps)
         mk = frame_mask(mask, j, F, taps)
@@ -286,14 +329,54 @@ def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=N
         G = D if taps is None else remap_adjoint(D, taps)
         for l in range(L):
             y, x = int(pos[l][j][0]), int(pos[l][j][1])
+            g_patch = np.zeros((F, F), np.complex128)
             for m in range(M):
                 chi = f4_adjoint(2.0 * G * Psi[l, m])
                 gP[l, m] += np.conj(s * patches[l]) * chi
-                gO[l][y:y + F, x:x + F] += np.conj(s * P[l, m]) * chi
+                g_patch += np.conj(s * P[l, m]) * chi
+            if delta is not None:
+                g_patch = f2_subpixel_adjoint(g_patch, delta[l][j])
+            gO[l][y:y + F, x:x + F] += g_patch
     return total, gO, gP
 
 
-def gradient_sigma_bg(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None):
+def gradient_delta(O, P, pos, Imeas, kind, eps, delta, sigma=None, bg=None, mask=None, taps=None, frames=None):
+    """Loss and its gradient with respect to the fractional scan offsets delta [L][J][2]
+    (the scan positions s_k are among the variables the paper optimises, Section
+    "Universal Ptychography Algorithm"; its position correction differentiates the
+    Fourier shift).  By the chain rule through the exit waves,
+    dL/d delta[l][j][a] = Re sum_r conj(g_p(r)) d p(r) / d delta_a with
+    g_p = sum_m conj(sigma P_lm) chi_jlm the gradient with respect to the shifted patch.
+    Returns (loss, g_delta [L][J][2], 0 for frames not requested)."""
+    L, M, F = P.shape[0], P.shape[1], P.shape[2]
+    J = pos.shape[1]
+    frames = range(J) if frames is None else frames
+    g_delta = np.zeros((L, J, 2))
+    total = 0.0
+    for j in frames:
+        s = _sigma(sigma, j)
+        patches, Psi = frame_fields(O, P, pos, j, sigma, delta)
+        I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
+        Ic = f5_measure(I_sum, bg, taps)
+        mk = frame_mask(mask, j, F, taps)
+        total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
+        with np.errstate(divide="ignore", invalid="ignore"):
+            D = np.where(mk, loss_derivative(Ic, Imeas[j], kind, eps), 0.0)
+        G = D if taps is None else remap_adjoint(D, taps)
+        for l in range(L):
+            g_patch = np.zeros((F, F), np.complex128)
+            for m in range(M):
+                chi = f4_adjoint(2.0 * G * Psi[l, m])
+                g_patch += np.conj(s * P[l, m]) * chi
+            window = f2_shift(O[l], pos[l][j], F)
+            for a in range(2):
+                dp = f2_subpixel_derivative(window, delta[l][j], a)
+                g_delta[l, j, a] = float(np.real(np.vdot(g_patch, dp)))
+    return total, g_delta
+
+
+def gradient_sigma_bg(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None,
+                      delta=None):
     """Loss and its gradient with respect to the power coefficients sigma_j and the
     background N (two of the model variables the paper lists as optimisable, Section
     "Universal Ptychography Algorithm", the paragraph after Eq. 2).
@@ -311,7 +394,7 @@ def gradient_sigma_bg(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=Non
     g_bg = np.zeros((F, F))
     total = 0.0
     for j in frames:
-        patches, Psi = frame_fields(O, P, pos, j, sigma)
+        patches, Psi = frame_fields(O, P, pos, j, sigma, delta)
         I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
         Ic = f5_measure(I_sum, bg, taps)
         mk = frame_mask(mask, j, F, taps)

@@ -465,3 +465,128 @@ def test_adam_second_step_against_hand_expansion():
     step2 = 0.1 * (m2 / (1 - 0.81)) / (math.sqrt(v2 / (1 - 0.999 ** 2)) + 1e-8)
     exp = 1.0 - 0.1 * g1 / (abs(g1) + 1e-8) - step2
     assert abs(th[0].real - exp) < 1e-14 and th[0].imag == 0.0
+
+
+# ----------------------------------------------------------------------------
+# f2 with fractional scan offsets (Fourier shift theorem) and the position gradient
+# ----------------------------------------------------------------------------
+
+def _subpixel_case(kind="poisson", remap=True, seed=41):
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=seed, remap=remap, loss=kind, with_sigma=True, with_bg=True)
+    taps = orc.remap_taps(w.F, 2e-3, 15e-6, math.radians(70)) if remap else None
+    rng = np.random.default_rng(seed + 1)
+    delta = rng.uniform(-0.5, 0.5, size=(w.L, w.J, 2))
+    return w, taps, delta
+
+
+def test_subpixel_shift_zero_and_whole_pixels():
+    """delta = 0 leaves the patch alone; a whole-pixel delta is a cyclic roll of the patch
+    (sampling at r + delta), in either axis and sign."""
+    rng = np.random.default_rng(50)
+    p = crandn(rng, 16, 16)
+    assert rel(orc.f2_subpixel(p, (0.0, 0.0)), p) < 1e-14
+    assert rel(orc.f2_subpixel(p, (1.0, 0.0)), np.roll(p, -1, axis=0)) < 1e-12
+    assert rel(orc.f2_subpixel(p, (0.0, -1.0)), np.roll(p, 1, axis=1)) < 1e-12
+    assert rel(orc.f2_subpixel(p, (-2.0, 3.0)), np.roll(np.roll(p, 2, axis=0), -3, axis=1)) < 1e-12
+
+
+def test_subpixel_shift_of_band_limited_plane_waves():
+    """A sum of in-band plane waves sampled on the grid, shifted by a fraction, equals the same
+    function sampled at the shifted points (the shift theorem is exact for it)."""
+    F = 16
+    n = np.arange(F)
+    rng = np.random.default_rng(51)
+    terms = [(int(a), int(b), complex(c)) for a, b, c in zip(rng.integers(-7, 8, 5), rng.integers(-7, 8, 5),
+                                                               crandn(rng, 5))]
+
+    def sample(dy, dx):
+        y = (n + dy)[:, None]
+        x = (n + dx)[None, :]
+        return sum(c * np.exp(2j * np.pi * (a * y + b * x) / F) for a, b, c in terms)
+
+    d = (0.37, -0.81)
+    assert rel(orc.f2_subpixel(sample(0.0, 0.0), d), sample(*d)) < 1e-12
+
+
+def test_subpixel_shift_is_unitary_composes_and_has_the_stated_adjoint():
+    rng = np.random.default_rng(52)
+    p, q = crandn(rng, 16, 16), crandn(rng, 16, 16)
+    d1, d2 = (0.3, -0.45), (-0.2, 0.7)
+    assert abs(np.linalg.norm(orc.f2_subpixel(p, d1)) - np.linalg.norm(p)) < 1e-12 * np.linalg.norm(p)
+    two = orc.f2_subpixel(orc.f2_subpixel(p, d1), d2)
+    assert rel(two, orc.f2_subpixel(p, (d1[0] + d2[0], d1[1] + d2[1]))) < 1e-12
+    lhs = np.vdot(q, orc.f2_subpixel(p, d1))
+    rhs = np.vdot(orc.f2_subpixel_adjoint(q, d1), p)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_subpixel_derivative_matches_finite_difference_of_the_shift():
+    rng = np.random.default_rng(53)
+    p = crandn(rng, 16, 16)
+    d = (0.21, -0.34)
+    h = 1e-6
+    for a in range(2):
+        dp = np.array(d)
+        dm = np.array(d)
+        dp[a] += h
+        dm[a] -= h
+        fd = (orc.f2_subpixel(p, dp) - orc.f2_subpixel(p, dm)) / (2 * h)
+        assert rel(orc.f2_subpixel_derivative(p, d, a), fd) < 1e-8
+
+
+def test_zero_offsets_reduce_to_the_integer_model():
+    w, taps, _ = _subpixel_case()
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps), 5)
+    zero = np.zeros((w.L, w.J, 2))
+    a = orc.gradient(w.O0, w.P0, w.pos, Ih, "poisson", 1e-3, w.sigma, w.bg, None, taps)
+    b = orc.gradient(w.O0, w.P0, w.pos, Ih, "poisson", 1e-3, w.sigma, w.bg, None, taps, delta=zero)
+    assert abs(a[0] - b[0]) <= 1e-13 * abs(a[0])
+    assert max(rel(x, y) for x, y in zip(a[1], b[1])) < 1e-12 and rel(a[2], b[2]) < 1e-12
+
+
+@pytest.mark.parametrize("kind", orc.LOSS_KINDS)
+@pytest.mark.parametrize("remap", [False, True])
+def test_position_gradient_matches_central_finite_differences(kind, remap):
+    w, taps, delta = _subpixel_case(kind, remap)
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps), 6)
+    args = (w.pos, Ih, kind, 1e-3)
+    kw = dict(sigma=w.sigma, bg=w.bg, taps=taps)
+    L0, gd = orc.gradient_delta(w.O0, w.P0, *args, delta, **kw)
+    assert abs(L0 - orc.loss(w.O0, w.P0, *args, delta=delta, **kw)) <= 1e-13 * abs(L0)
+    h = 1e-6
+    noise = 50 * 2.2e-16 * abs(L0) / h
+    rng = np.random.default_rng(54)
+    for _ in range(6):
+        l, j, a = int(rng.integers(w.L)), int(rng.integers(w.J)), int(rng.integers(2))
+        dp, dm = delta.copy(), delta.copy()
+        dp[l, j, a] += h
+        dm[l, j, a] -= h
+        fd = (orc.loss(w.O0, w.P0, *args, delta=dp, **kw) - orc.loss(w.O0, w.P0, *args, delta=dm, **kw)) / (2 * h)
+        assert abs(fd - gd[l, j, a]) <= 1e-6 * abs(gd[l, j, a]) + noise, (l, j, a, fd, gd[l, j, a])
+
+
+def test_object_and_probe_gradients_with_offsets_match_finite_differences():
+    w, taps, delta = _subpixel_case("amplitude", True)
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps), 7)
+    args = (w.pos, Ih, "amplitude", 1e-3, w.sigma, w.bg, None, taps)
+    _, gO, gP = orc.gradient(w.O0, w.P0, *args, delta=delta)
+    rng = np.random.default_rng(55)
+    dO = [crandn(rng, *o.shape) for o in w.O0]
+    dP = crandn(rng, *w.P0.shape)
+    h = 1e-6
+    Lp = orc.loss([o + h * d for o, d in zip(w.O0, dO)], w.P0 + h * dP, *args, delta=delta)
+    Lm = orc.loss([o - h * d for o, d in zip(w.O0, dO)], w.P0 - h * dP, *args, delta=delta)
+    fd = (Lp - Lm) / (2 * h)
+    an = sum(np.real(np.vdot(g, d)) for g, d in zip(gO, dO)) + np.real(np.vdot(gP, dP))
+    assert abs(fd - an) < 1e-6 * abs(an)
+
+
+def test_position_gradient_vanishes_at_noiseless_truth_and_for_frames_not_requested():
+    w, taps, delta = _subpixel_case()
+    Ih = orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps, delta=delta)
+    L, gd = orc.gradient_delta(w.O_true, w.P_true, w.pos, Ih, "poisson", 0.0, delta, w.sigma, w.bg, None, taps)
+    assert abs(L) < 1e-18 * float(Ih.sum()) and np.abs(gd).max() < 1e-10
+    Ih2 = syn.poisson_measure(Ih, 8)
+    _, gd2 = orc.gradient_delta(w.O0, w.P0, w.pos, Ih2, "poisson", 1e-3, delta, w.sigma, w.bg, None, taps,
+                                frames=[1, 4])
+    assert np.all(gd2[:, [0, 2, 3, 5, 6, 7, 8], :] == 0.0) and np.abs(gd2[:, [1, 4], :]).max() > 0
