@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="config5: HBM budget of the server")
     ap.add_argument("--no-plain", action="store_true", help="config5: skip the plain one-site-at-a-time run")
     ap.add_argument("--plain", action="store_true", help="time the plain unfused step instead of the fused one")
+    ap.add_argument("--corrections-steps", type=int, default=20,
+                    help="steps timed with position (and power/background) correction on (0 = skip)")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the reduced serving stream appended to the default line (0 = none)")
     ap.add_argument("--tick-evals", type=int, default=32768,
@@ -371,6 +373,44 @@ def run_ours(args, rank: int, world: int):
                "h2d_bytes_per_step": int(Ih_pinned.numel() * 4), "d2h_bytes_per_step": 8,
                "note": "pinned host I_meas copied to the GPU every step; loss read back every step"}
 
+    # ---- the step with correction of further variables (the paper's Fig. 3 comparison) ----
+    corrections = None
+    if args.corrections_steps > 0 and not args.plain and not args.graph:
+        def timed(fn, n):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for k in range(n):
+                flush.fill_(float(k))
+                a0.record(stream)
+                fn()
+                a1.record(stream)
+                a1.synchronize()
+                tot += a0.elapsed_time(a1)
+            return tot / n
+        rng = np.random.default_rng(7)
+        delta = torch.as_tensor(rng.uniform(-0.5, 0.5, size=(w.L, w.J, 2)).astype(np.float32), device=dev)
+        sig = torch.ones(w.J, dtype=torch.float32, device=dev)
+        bgt = torch.ones(w.F, w.F, dtype=torch.float32, device=dev)
+        O2, P2 = O.clone(), P.clone()
+        base_ms = timed(lambda: plan.step(st, O2, P2, Im, loss_out=loss), args.corrections_steps)
+        plan.set_offsets(delta)
+        st_pos = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2)
+        pos_ms = timed(lambda: plan.step(st_pos, O2, P2, Im, loss_out=loss), args.corrections_steps)
+        st_all = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2, lr_sigma=1e-2, lr_bg=1e-2)
+        all_ms = timed(lambda: plan.step(st_all, O2, P2, Im, sig, bgt, loss_out=loss), args.corrections_steps)
+        plan.set_offsets(None)
+        corrections = {
+            "steps": args.corrections_steps,
+            "object_probe": {"ms_per_step": base_ms, "evals_per_s": evals / (base_ms / 1e3)},
+            "plus_positions": {"ms_per_step": pos_ms, "evals_per_s": evals / (pos_ms / 1e3),
+                               "relative_time": pos_ms / base_ms},
+            "plus_positions_power_background": {"ms_per_step": all_ms, "evals_per_s": evals / (all_ms / 1e3),
+                                                "relative_time": all_ms / base_ms},
+            "note": "fractional scan offsets (Fourier shift) optimised by Adam in the same step; uniform(-0.5, 0.5) px"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, t1, _ = oracle_evals_per_s(w, 1)
@@ -409,7 +449,7 @@ def run_ours(args, rank: int, world: int):
                 "roofline": roof, "step_flop_rate_tflops": step_flops / (t_ms / args.steps / 1e3) / 1e12,
                 "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
-                "serving": serving}
+                "serving": serving, "corrections": corrections}
         print(json.dumps(line))
     plan.close()
     if dist:

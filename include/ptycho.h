@@ -140,6 +140,10 @@ typedef struct {
   float lr_bg;              /* > 0: ptycho_step updates bg [F][F] in place              */
   float* m_sigma; float* v_sigma;   /* [J], required when lr_sigma > 0                  */
   float* m_bg; float* v_bg;         /* [F*F], required when lr_bg > 0                   */
+  /* Optional: the fractional scan offsets registered with ptycho_plan_set_offsets are
+   * optimised too (the paper refines the scan positions s_k with the other variables). */
+  float lr_delta;                   /* > 0: ptycho_step updates the offsets in place          */
+  float* m_delta; float* v_delta;   /* [L*J*2], required when lr_delta > 0                    */
 } ptycho_adam_t;
 
 /* Validates the geometry and every scan position (PTYCHO_ERANGE names an out-of-object
@@ -186,9 +190,9 @@ int ptycho_adjoint(ptycho_plan_t* plan, const float* O, const float* P, const fl
                    const int32_t* batch_idx, int nbatch, float* gO, float* gP, double* loss_dev,
                    void* stream);
 
-/* ptycho_adjoint that also returns the gradients with respect to the power coefficients
- * and the background (the paper's sigma_k and N(rho), Eq. 1), each optional (NULL = not
- * computed):
+/* ptycho_adjoint that also returns the gradients with respect to the power coefficients,
+ * the background and the fractional scan offsets (the paper's sigma_k, N(rho) and s_k,
+ * Eq. 1), each optional (NULL = not computed):
  *   g_sigma [J] OVERWRITTEN: dL/dsigma_j for every position in the call, 0 for the others.
  *           Computed from the intensities: sigma_j enters every exit wave of frame j as a
  *           real factor and the DFT is unitary, so dL/dsigma_j = (2 / sigma_j) times the
@@ -197,11 +201,34 @@ int ptycho_adjoint(ptycho_plan_t* plan, const float* O, const float* P, const fl
  *   g_bg    [F][F] OVERWRITTEN: dL/dN on the model grid (N is added before the remap),
  *           the sum over the call's positions of R^T(mask dL/dI); deterministic for a
  *           given plan (per-stream partial sums added in a fixed order).
+ *   g_delta [L][J][2] OVERWRITTEN: dL/ddelta[l][j] (rows, columns) for the positions in the
+ *           call, 0 for the others; requires offsets registered with
+ *           ptycho_plan_set_offsets (PTYCHO_EINVAL otherwise).  Computed in the Fourier
+ *           domain: (1/F^2) Re sum_k conj(Ghat(k)) 2 pi i f(k) Q(k), Ghat the DFT of the
+ *           gradient with respect to the shifted patch, Q the ramp times the DFT of the
+ *           integer window, f in cycles per pixel.
  * Other arguments as for ptycho_adjoint. */
 int ptycho_adjoint_ex(ptycho_plan_t* plan, const float* O, const float* P, const float* sigma,
                       const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
                       const int32_t* batch_idx, int nbatch, float* gO, float* gP, float* g_sigma,
-                      float* g_bg, double* loss_dev, void* stream);
+                      float* g_bg, float* g_delta, double* loss_dev, void* stream);
+
+/* Fractional scan offsets (f2 by the Fourier shift theorem, the paper's differentiable
+ * scanning shift; Section "Benchmarking with state-of-art ...").  Registers delta, a DEVICE
+ * array [L][J][2] of float32 (rows, then columns, in object pixels of wavelength l) that
+ * every later compute call on this plan adds to the integer positions of the geometry: the
+ * F x F window at pos[l][j] is resampled at r + delta[l][j] as F2^-1[ramp * F2 window],
+ * ramp(k) = exp(2 pi i (f(k_y) d_y + f(k_x) d_x)), f in cycles per pixel with the Nyquist
+ * index at -1/2; the window is taken as one period (its edge rows and columns wrap, where
+ * the probe is negligible).  Any |delta| is accepted; large offsets belong in the integer
+ * positions of a new plan.  The array stays owned by the caller and must stay alive while
+ * registered; ptycho_step updates it in place when the Adam state has lr_delta > 0.
+ * delta = NULL clears the registration (integer positions again).  The first registration
+ * allocates the shift workspaces (3 x nsets x B x L x F^2 complex64).  PTYCHO_EUNSUPPORTED
+ * when the plan processes a position's modes in chunks or T*M > 256 (T = 4, 8, 16, 16
+ * threads per row for F = 64, 128, 256, 512); PTYCHO_ENOMEM when the workspaces do not fit;
+ * the plain baseline (ptycho_plain_step) rejects plans with offsets. */
+int ptycho_plan_set_offsets(ptycho_plan_t* plan, float* delta);
 
 /* One optimisation step on a batch of positions ("per batch" updates, Fig. 2 caption):
  * ptycho_adjoint into plan-owned gradient buffers, then Adam on O (lr_O) and P (lr_P) in
@@ -295,7 +322,8 @@ int64_t ptycho_server_used_bytes(const ptycho_server_t* server);
 #define PTYCHO_K_LOSS_REDUCE 6   /* FP64 loss reduction                                   */
 #define PTYCHO_K_ADAM 7          /* Adam update                                          */
 #define PTYCHO_K_REMAP_ADJ 8     /* R^T of the tilted-plane remap                         */
-#define PTYCHO_NUM_KERNELS 9
+#define PTYCHO_K_SHIFT 9         /* Fourier shift of fractional scan offsets + dL/ddelta  */
+#define PTYCHO_NUM_KERNELS 10
 int ptycho_plan_profile(ptycho_plan_t* plan, int enable);
 int ptycho_plan_profile_read(ptycho_plan_t* plan, double* ms, int64_t* launches);
 const char* ptycho_kernel_name(int kind);

@@ -35,6 +35,7 @@ class Adam(ctypes.Structure):
         ("lr_sigma", ctypes.c_float), ("lr_bg", ctypes.c_float),
         ("m_sigma", ctypes.c_void_p), ("v_sigma", ctypes.c_void_p), ("m_bg", ctypes.c_void_p),
         ("v_bg", ctypes.c_void_p),
+        ("lr_delta", ctypes.c_float), ("m_delta", ctypes.c_void_p), ("v_delta", ctypes.c_void_p),
     ]
 
 
@@ -60,7 +61,8 @@ SIGNATURES = [
     ("ptycho_forward", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ptycho_loss", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     ("ptycho_adjoint", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP]),
-    ("ptycho_adjoint_ex", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ptycho_adjoint_ex", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ptycho_plan_set_offsets", _I, [_VP, _VP]),
     ("ptycho_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     ("ptycho_plan_status", _I, [_VP, c_int32_p]),
     ("ptycho_plan_profile", _I, [_VP, _I]),
@@ -79,7 +81,7 @@ SIGNATURES = [
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 
-NUM_KERNELS = 9
+NUM_KERNELS = 10
 _LIB = None
 
 

@@ -237,8 +237,22 @@ class Plan:
         _check(rc, "ptycho_adjoint")
         return loss_out, gO, gP
 
+    def set_offsets(self, delta):
+        """ptycho_plan_set_offsets: register fractional scan offsets (a contiguous float32
+        device tensor of L*J*2 elements, [L, J, 2] rows then columns) or clear them (None).
+        The plan keeps a reference to the tensor while it is registered."""
+        if delta is not None:
+            self._f32(delta, self.L * self.J * 2, "delta")
+        _check(_native.lib().ptycho_plan_set_offsets(self._h_plan, _ptr(delta)), "ptycho_plan_set_offsets")
+        self._delta = delta
+
+    @property
+    def offsets(self):
+        return getattr(self, "_delta", None)
+
     def adjoint_ex(self, O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, stream=None):
-        """ptycho_adjoint_ex: (loss, grad O, grad P, grad sigma [J], grad bg [F, F])."""
+        """ptycho_adjoint_ex: (loss, grad O, grad P, grad sigma [J], grad bg [F, F],
+        grad delta [L, J, 2] or None when no offsets are registered)."""
         FF = self.F * self.F
         Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
         m, mpf = self._mask(mask)
@@ -247,14 +261,16 @@ class Plan:
         gP = torch.empty(P.shape, dtype=torch.complex64, device=self.device)
         gs = torch.empty(self.J, dtype=torch.float32, device=self.device)
         gb = torch.empty(self.F, self.F, dtype=torch.float32, device=self.device)
+        gd = torch.empty(self.L, self.J, 2, dtype=torch.float32, device=self.device) if self.offsets is not None \
+            else None
         loss_out = torch.zeros(1, dtype=torch.float64, device=self.device)
         rc = _native.lib().ptycho_adjoint_ex(self._h_plan, _ptr(Or), _ptr(Pr), _ptr(self._f32(sigma, self.J, "sigma")),
                                              _ptr(self._f32(bg, FF, "bg")),
                                              _ptr(self._f32(Imeas, self.J * FF, "Imeas")), _ptr(m), mpf, _ptr(bt), nb,
-                                             _ptr(gO), _ptr(gP), _ptr(gs), _ptr(gb), _ptr(loss_out),
+                                             _ptr(gO), _ptr(gP), _ptr(gs), _ptr(gb), _ptr(gd), _ptr(loss_out),
                                              _stream_handle(stream))
         _check(rc, "ptycho_adjoint_ex")
-        return loss_out, gO, gP, gs, gb
+        return loss_out, gO, gP, gs, gb, gd
 
     def step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, loss_out=None,
              stream=None):
@@ -297,7 +313,8 @@ class AdamState:
     """Adam moments for O and P (device tensors, 2 floats per complex element)."""
 
     def __init__(self, plan: Plan, lr_O: float, lr_P: float, beta1: float = 0.9, beta2: float = 0.999,
-                 eps: float = 1e-8, device_counter: bool = False, lr_sigma: float = 0.0, lr_bg: float = 0.0):
+                 eps: float = 1e-8, device_counter: bool = False, lr_sigma: float = 0.0, lr_bg: float = 0.0,
+                 lr_delta: float = 0.0):
         dev = plan.device
         # optional: sigma [J] and the background [F, F] are optimised too (updated in place by
         # Plan.step, which then needs them as float32 device tensors)
@@ -306,6 +323,10 @@ class AdamState:
         self.v_sigma = torch.zeros_like(self.m_sigma) if lr_sigma > 0 else None
         self.m_bg = torch.zeros(plan.F * plan.F, dtype=torch.float32, device=dev) if lr_bg > 0 else None
         self.v_bg = torch.zeros_like(self.m_bg) if lr_bg > 0 else None
+        # optional: the registered fractional scan offsets ([L, J, 2]) are optimised too
+        self.lr_delta = lr_delta
+        self.m_delta = torch.zeros(plan.L * plan.J * 2, dtype=torch.float32, device=dev) if lr_delta > 0 else None
+        self.v_delta = torch.zeros_like(self.m_delta) if lr_delta > 0 else None
         # with a device step counter a captured CUDA graph of Plan.step can be replayed
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=dev) if device_counter else None
         self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps = lr_O, lr_P, beta1, beta2, eps
@@ -321,8 +342,8 @@ class AdamState:
         s.mO, s.vO = self.mO.data_ptr(), self.vO.data_ptr()
         s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
         s.t_dev = None if self.t_dev is None else self.t_dev.data_ptr()
-        s.lr_sigma, s.lr_bg = self.lr_sigma, self.lr_bg
-        for name in ("m_sigma", "v_sigma", "m_bg", "v_bg"):
+        s.lr_sigma, s.lr_bg, s.lr_delta = self.lr_sigma, self.lr_bg, self.lr_delta
+        for name in ("m_sigma", "v_sigma", "m_bg", "v_bg", "m_delta", "v_delta"):
             t = getattr(self, name)
             setattr(s, name, None if t is None else t.data_ptr())
         return s

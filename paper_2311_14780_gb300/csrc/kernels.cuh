@@ -53,6 +53,8 @@ struct KArgs {
   int* status;                   // device status word (bit 0: a position index was out of range)
   int box[kMaxL][4];             // per wavelength: rows [box0, box2) x cols [box1, box3) covered by
                                  // the batch's patches (the whole object when not known on the host)
+  const float2* patch;           // [B][L][F][F] object patches shifted by fractional offsets, or null
+                                 // (the row passes then gather the patch from O at the integer position)
 };
 
 // Programmatic dependent launch: the pipeline launches each kernel so that it may start
@@ -125,7 +127,8 @@ k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   if (j < 0) return;                                  // uniform over the block
   const int y = a.pos[(l * a.J + j) * 2], x = a.pos[(l * a.J + j) * 2 + 1];
   const float s = sigma_of(a, j);
-  const float2* Orow = O + a.obj_off[l] + (long long)(y + r) * a.obj_w[l] + x;
+  const float2* Orow = a.patch ? a.patch + (((long long)b * a.L + l) * F + r) * F
+                               : O + a.obj_off[l] + (long long)(y + r) * a.obj_w[l] + x;
   float2 p[N2];
 #pragma unroll
   for (int n2 = 0; n2 < N2; ++n2) p[n2] = cscale(__ldg(Orow + t + N1 * n2), s);
@@ -978,7 +981,10 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
     float2* dst = Sst + (buf * V + vec) * RR;
 #pragma unroll
     for (int k = 0; k < F / (2 * T); ++k) cp_async16(dst + 2 * (t + T * k), row + 2 * (t + T * k));
-    prefetch_orows<F>(Ol, Wl, spos[b], row0, rpb, Ost + buf * rpb * F);
+    if (a.patch)
+      prefetch_orows<F>(a.patch + ((long long)b * a.L + l) * F * F, F, make_int2(0, 0), row0, rpb, Ost + buf * rpb * F);
+    else
+      prefetch_orows<F>(Ol, Wl, spos[b], row0, rpb, Ost + buf * rpb * F);
     cp_async_commit();
   };
   float2 acc[N2];

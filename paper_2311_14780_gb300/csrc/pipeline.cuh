@@ -88,6 +88,11 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_fwd_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_cols<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_cols<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = set_cols_smem<F, 0>();
   if (e == cudaSuccess) e = set_cols_smem<F, 4>();
   if (e != cudaSuccess) return PTYCHO_ECUDA;
@@ -110,9 +115,13 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const bool obj_atomic = (p.flags & PTYCHO_FLAG_OBJ_GRAD_ATOMIC) != 0;
   // all modes of a wavelength per adjoint row block; with several position splits the probe
   // gradient is summed per split and the splits are added in order at the end
-  const bool adj_l = p.adj_l && !obj_atomic && p.nchunks == 1;
+  // fractional scan offsets: the Fourier-shift passes, the fused row adjoint (it forms the
+  // mode-summed object-gradient patch that the adjoint shift transforms)
+  const bool shifted = p.d_delta != nullptr;
+  if (shifted && (p.nchunks != 1 || !p.adj_l_ok)) return PTYCHO_EUNSUPPORTED;
+  const bool adj_l = (p.adj_l && !obj_atomic && p.nchunks == 1) || shifted;
   const bool col_staged = p.col_staged && p.nchunks == 1;
-  const bool fwd_l = p.fwd_l && p.nchunks == 1;
+  const bool fwd_l = p.fwd_l && p.nchunks == 1 && !shifted;
   const bool narrow = (p.flags & PTYCHO_FLAG_NARROW_COLUMNS) != 0;
   const int nsplit = adj_l ? p.nsplit_adj : 1;
   float2* gPs = nsplit > 1 ? p.d_gPs : c.gP;
@@ -208,6 +217,23 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       max_tiles = tiles > max_tiles ? tiles : max_tiles;
     }
     // forward: all chunks accumulate the model intensity
+    // fractional offsets: shift the batch's object windows into the patch buffer
+    const long long set_P = (long long)p.B * p.L * FF;
+    ShiftArgs sh{};
+    if (shifted) {
+      sh.delta = p.d_delta;
+      sh.T = p.d_shT + set * set_P;
+      sh.Q = p.d_shQ + set * set_P;
+      float2* Pt = p.d_shP + set * set_P;
+      const dim3 rgrid(F / RowCfg<F>::RPB, p.L, a.nb), cgrid(F / ColCfg<F>::W, p.L, a.nb);
+      sh.dst = sh.T; sh.dst_b = (long long)p.L * FF; sh.dst_l = FF; sh.scale = 1.0f;
+      PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_rows<F, false, true>, rgrid, row_blk, RowCfg<F>::smem, cs, c.O, a, sh));
+      PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_cols<F, false>, cgrid, col_blk, ColCfg<F>::smem_xch, cs, a, sh));
+      sh.src = sh.T; sh.src_b = (long long)p.L * FF; sh.src_l = FF;
+      sh.dst = Pt; sh.scale = 1.0f / (float)FF;
+      PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_rows<F, true, false>, rgrid, row_blk, RowCfg<F>::smem, cs, c.O, a, sh));
+      a.patch = Pt;
+    }
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
@@ -271,6 +297,18 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
                               row_adj_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, gPs, (long long)p.P_numel, a,
                               p.rpb_adj, nsplit));
         if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+        if (shifted) {                                // adjoint shift of the mode-summed patch gradients
+          const dim3 rgrid(F / RowCfg<F>::RPB, p.L, a.nb), cgrid(F / ColCfg<F>::W, p.L, a.nb);
+          sh.src = S; sh.src_b = (long long)p.C * FF; sh.src_l = (long long)p.M * FF;
+          sh.dst = sh.T; sh.dst_b = (long long)p.L * FF; sh.dst_l = FF; sh.scale = 1.0f;
+          PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_rows<F, false, false>, rgrid, row_blk, RowCfg<F>::smem, cs, c.O, a, sh));
+          sh.dpart = c.g_delta ? p.d_dpart : nullptr;
+          PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_cols<F, true>, cgrid, col_blk, ColCfg<F>::smem_xch, cs, a, sh));
+          sh.src = sh.T; sh.src_b = (long long)p.L * FF; sh.src_l = FF;
+          sh.dst = S; sh.dst_b = (long long)p.C * FF; sh.dst_l = (long long)p.M * FF; sh.scale = 1.0f / (float)FF;
+          PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_rows<F, true, false>, rgrid, row_blk, RowCfg<F>::smem, cs, c.O, a, sh));
+          sh.dpart = nullptr;
+        }
         if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_og[(k - 1) % nsets], 0) != cudaSuccess)
           return PTYCHO_ECUDA;
         PTY_LAUNCH(p, kObjGrad, cs, launch_pdl(k_obj_grad_l<F>, dim3(max_tiles, p.L), 256, 0, cs, S, c.gO, a));
@@ -299,6 +337,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   if (grad && nsplit > 1)
     PTY_LAUNCH(p, kRowAdj, st,
                launch_pdl(k_sum_splits, dim3(4 * p.sms), 256, 0, st, (const float2*)gPs, nsplit, p.P_numel, c.gP));
+  if (grad && c.g_delta)
+    PTY_LAUNCH(p, kShift, st,
+               launch_pdl(k_delta_grad, dim3((p.L * p.J + 255) / 256), 256, 0, st, (const int32_t*)c.bidx, c.nbatch,
+                          p.L, p.J, (const double*)p.d_dpart, F / ColCfg<F>::W, c.g_delta));
   if (grad && c.g_sigma)
     PTY_LAUNCH(p, kLossReduce, st,
                launch_pdl(k_sigma_grad, dim3((p.J + 255) / 256), 256, 0, st, (const int32_t*)c.bidx, c.nbatch, p.J,

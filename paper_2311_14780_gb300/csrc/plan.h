@@ -8,6 +8,7 @@
 
 #include "../../include/ptycho.h"
 #include "kernels.cuh"
+#include "shift.cuh"
 
 struct ptycho_plan {
   int dev = 0;
@@ -27,6 +28,7 @@ struct ptycho_plan {
   // adjoint row pass over all modes of a wavelength per block (k_row_adj_l): rows per block,
   // position splits (each with its own probe-gradient buffer when nsplit > 1)
   int adj_l = 0, rpb_adj = 1, nsplit_adj = 1;
+  int adj_l_ok = 0;                            // k_row_adj_l can run (all modes fit a block and the scratch)
   // forward row pass over all modes of a wavelength per block (k_row_fwd_l), same rows per block
   int fwd_l = 0, nsplit_fwd = 1;
   // staged column passes (k_col_fwd_s / k_col_adj_s): one block per W columns of a position
@@ -67,6 +69,14 @@ struct ptycho_plan {
   float2* d_gP = nullptr;
   float2* d_gPs = nullptr;                     // [nsplit_adj][L][M][F][F] probe-gradient partials
   int* d_status = nullptr;                     // device status word, see ptycho_plan_status
+  // fractional scan offsets (ptycho_plan_set_offsets): the caller's [L][J][2] array and the
+  // per-set workspaces of the Fourier shift (allocated on first registration)
+  float* d_delta = nullptr;
+  float2* d_shT = nullptr;                     // [nsets][B][L][F][F] transform workspace
+  float2* d_shQ = nullptr;                     // [nsets][B][L][F][F] ramp * spectrum of the windows
+  float2* d_shP = nullptr;                     // [nsets][B][L][F][F] shifted patches
+  double* d_dpart = nullptr;                   // [J][L][F/W][2] position-gradient partials
+  float* d_gdelta = nullptr;                   // [L][J][2] position gradient (ptycho_step)
 
   // TMA tensor maps of each scratch set, viewed as [B*C*F rows][F columns] of 8-byte elements
   // with a W x min(F, 256) box (column passes); has_tma = 0 falls back to plain loads
@@ -102,11 +112,12 @@ struct CallArgs {
   float2* gP;
   float* g_sigma;          // [J] or null
   float* g_bg;             // [F][F] or null
+  float* g_delta;          // [L][J][2] or null (requires registered offsets)
   double* loss;
 };
 
 // Kernel kinds reported by ptycho_plan_profile_read (order matches PTYCHO_K_* in ptycho.h).
-enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kRemapAdj, kNumKinds };
+enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kRemapAdj, kShift, kNumKinds };
 
 // Records the start event of a profiled launch (no-op unless profiling); returns the pair index.
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);

@@ -48,6 +48,26 @@ k_sigma_grad(const int32_t* __restrict__ bidx, int nbatch, int J, const double* 
   g[j] = sj != 0.f ? (float)(2.0 * s / (double)sj) : 0.f;
 }
 
+__global__ void __launch_bounds__(256)
+k_delta_grad(const int32_t* __restrict__ bidx, int nbatch, int L, int J, const double* __restrict__ dpart,
+             int nstrips, float* __restrict__ g_delta) {
+  pdl_wait();
+  const int e = blockIdx.x * 256 + threadIdx.x;       // e = l*J + j
+  if (e >= L * J) return;
+  const int l = e / J, j = e % J;
+  double sy = 0.0, sx = 0.0;
+  for (int i = 0; i < nbatch; ++i) {
+    if (__ldg(bidx + i) != j) continue;
+    const double* d = dpart + ((long long)i * L + l) * nstrips * 2;
+    for (int k = 0; k < nstrips; ++k) {
+      sy += d[2 * k];
+      sx += d[2 * k + 1];
+    }
+  }
+  g_delta[2 * e] = (float)sy;
+  g_delta[2 * e + 1] = (float)sx;
+}
+
 // out[i] = sum over the probe-gradient splits, in split order, of part[s][i].
 __global__ void __launch_bounds__(256)
 k_sum_splits(const float2* __restrict__ part, int nsplit, long long n, float2* __restrict__ out) {
@@ -174,7 +194,8 @@ void free_plan(ptycho_plan* p) {
   }
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
-                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs};
+                  p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs, p->d_shT, p->d_shQ, p->d_shP,
+                  p->d_dpart, p->d_gdelta};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -417,7 +438,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     }
     // measured: at F = 512 the fused kernel's registers (two 32-value rows per thread) cost
     // more occupancy than the probe reuse saves, so F = 512 keeps one block per mode
-    if (p->store && !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) && T * g->M <= 256 && F <= 256) {
+    if (p->store && T * g->M <= 256) {
       int rpb = 1;
       while (2 * rpb * T * g->M <= 128 && 2 * rpb <= F) rpb *= 2;
       switch (F) {
@@ -427,7 +448,8 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
         default: smem = ptycho::row_adj_l_smem<512>(g->M, rpb); break;
       }
       if (smem <= ptycho::kRowAdjLSmemMax) {
-        p->adj_l = 1;
+        p->adj_l_ok = 1;
+        p->adj_l = !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) && F <= 256;
         p->rpb_adj = rpb;
         // enough blocks for three per SM: split the batch's positions, each split summing its
         // probe gradient into a buffer of its own (bounded to 512 MB in all)
@@ -476,7 +498,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   rc = rc ? rc : dalloc(p, &p->d_gbg, FF);
   rc = rc ? rc : dalloc(p, &p->d_gO, p->O_numel);
   rc = rc ? rc : dalloc(p, &p->d_gP, p->P_numel);
-  if (p->nsplit_adj > 1) rc = rc ? rc : dalloc(p, &p->d_gPs, (long long)p->nsplit_adj * p->P_numel);
+  if (p->adj_l_ok && p->nsplit_adj > 1) rc = rc ? rc : dalloc(p, &p->d_gPs, (long long)p->nsplit_adj * p->P_numel);
   rc = rc ? rc : dalloc(p, &p->d_status, 1);
   if (!rc && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = PTYCHO_ECUDA;
   if (rc) { free_plan(p); return rc; }
@@ -574,7 +596,7 @@ int ptycho_plan_profile_read(ptycho_plan_t* p, double* ms, int64_t* launches) {
 
 const char* ptycho_kernel_name(int kind) {
   static const char* names[] = {"row_fwd", "col_fwd", "loss", "col_adj", "row_adj", "obj_grad", "loss_reduce", "adam",
-                                "remap_adj"};
+                                "remap_adj", "shift"};
   return (kind >= 0 && kind < ptycho::kNumKinds) ? names[kind] : "unknown";
 }
 
@@ -605,6 +627,43 @@ int ptycho_forward(ptycho_plan_t* p, const float* O, const float* P, const float
   return dispatch(p, c, (cudaStream_t)stream);
 }
 
+int ptycho_plan_set_offsets(ptycho_plan_t* p, float* delta) {
+  if (!p) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  if (!delta) {
+    p->d_delta = nullptr;
+    return PTYCHO_OK;
+  }
+  if (!p->store || !p->adj_l_ok) return PTYCHO_EUNSUPPORTED;
+  if (!p->d_shT) {
+    const long long n = (long long)p->nsets * p->B * p->L * p->F * p->F;
+    int W = 0;
+    switch (p->F) {
+      case 64: W = ptycho::ColCfg<64>::W; break;
+      case 128: W = ptycho::ColCfg<128>::W; break;
+      case 256: W = ptycho::ColCfg<256>::W; break;
+      default: W = ptycho::ColCfg<512>::W; break;
+    }
+    rc = dalloc(p, &p->d_shT, n);
+    rc = rc ? rc : dalloc(p, &p->d_shQ, n);
+    rc = rc ? rc : dalloc(p, &p->d_shP, n);
+    rc = rc ? rc : dalloc(p, &p->d_dpart, (long long)p->J * p->L * (p->F / W) * 2);
+    rc = rc ? rc : dalloc(p, &p->d_gdelta, 2ll * p->L * p->J);
+    if (rc) {                                         // leave the plan as it was
+      void* bufs[] = {p->d_shT, p->d_shQ, p->d_shP, p->d_dpart, p->d_gdelta};
+      for (void* q : bufs)
+        if (q) cudaFree(q);
+      p->d_shT = p->d_shQ = p->d_shP = nullptr;
+      p->d_dpart = nullptr;
+      p->d_gdelta = nullptr;
+      return rc;
+    }
+  }
+  p->d_delta = delta;
+  return PTYCHO_OK;
+}
+
 int ptycho_loss(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
                 const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
                 int nbatch, double* loss_dev, void* stream) {
@@ -630,14 +689,15 @@ int ptycho_adjoint(ptycho_plan_t* p, const float* O, const float* P, const float
                    const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
                    int nbatch, float* gO, float* gP, double* loss_dev, void* stream) {
   return ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch, gO, gP, nullptr,
-                           nullptr, loss_dev, stream);
+                           nullptr, nullptr, loss_dev, stream);
 }
 
 int ptycho_adjoint_ex(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
                       const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
-                      int nbatch, float* gO, float* gP, float* g_sigma, float* g_bg, double* loss_dev,
-                      void* stream) {
+                      int nbatch, float* gO, float* gP, float* g_sigma, float* g_bg, float* g_delta,
+                      double* loss_dev, void* stream) {
   if (!p || !O || !P || !I_meas || !gO || !gP) return PTYCHO_EINVAL;
+  if (g_delta && !p->d_delta) return PTYCHO_EINVAL;   // a position gradient needs registered offsets
   int rc = check_device(p);
   if (rc) return rc;
   CallArgs c{};
@@ -653,6 +713,7 @@ int ptycho_adjoint_ex(ptycho_plan_t* p, const float* O, const float* P, const fl
   c.gP = reinterpret_cast<float2*>(gP);
   c.g_sigma = g_sigma;
   c.g_bg = g_bg;
+  c.g_delta = g_delta;
   c.loss = loss_dev;
   rc = fill_batch(p, c, batch_idx, nbatch);
   if (rc) return rc;
@@ -664,16 +725,19 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
                 int nbatch, double* loss_dev, void* stream) {
   if (!p || !s || !O || !P || !I_meas || !s->mO || !s->vO || !s->mP || !s->vP) return PTYCHO_EINVAL;
   if (!(s->beta1 >= 0.f && s->beta1 < 1.f && s->beta2 >= 0.f && s->beta2 < 1.f && s->eps >= 0.f)) return PTYCHO_EINVAL;
-  const bool opt_sigma = s->lr_sigma > 0.f, opt_bg = s->lr_bg > 0.f;
+  const bool opt_sigma = s->lr_sigma > 0.f, opt_bg = s->lr_bg > 0.f, opt_delta = s->lr_delta > 0.f;
   if (opt_sigma && (!sigma || !s->m_sigma || !s->v_sigma)) return PTYCHO_EINVAL;
   if (opt_bg && (!bg || !s->m_bg || !s->v_bg)) return PTYCHO_EINVAL;
+  if (opt_delta && (!p->d_delta || !s->m_delta || !s->v_delta)) return PTYCHO_EINVAL;
   int rc = ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
                              reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP),
-                             opt_sigma ? p->d_gsig : nullptr, opt_bg ? p->d_gbg : nullptr, loss_dev, stream);
+                             opt_sigma ? p->d_gsig : nullptr, opt_bg ? p->d_gbg : nullptr,
+                             opt_delta ? p->d_gdelta : nullptr, loss_dev, stream);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;
   const long long FF = (long long)p->F * p->F;
+  const long long nD = 2ll * p->L * p->J;
   const int grid = 4 * p->sms;
   if (s->t_dev) {
     // device step counter: the update can be captured once and replayed
@@ -694,6 +758,11 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
     if (opt_bg) {
       ptycho::k_adam_dev<<<(int)((FF + 255) / 256), 256, 0, st>>>(bg, p->d_gbg, s->m_bg, s->v_bg, FF, s->lr_bg,
                                                                    s->beta1, s->beta2, s->eps, s->t_dev);
+      ++p->last_launches;
+    }
+    if (opt_delta) {
+      ptycho::k_adam_dev<<<(int)((nD + 255) / 256), 256, 0, st>>>(p->d_delta, p->d_gdelta, s->m_delta, s->v_delta, nD,
+                                                                   s->lr_delta, s->beta1, s->beta2, s->eps, s->t_dev);
       ++p->last_launches;
     }
     if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
@@ -723,6 +792,12 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
   if (opt_bg) {
     ptycho::k_adam<<<(int)((FF + 255) / 256), 256, 0, st>>>(bg, p->d_gbg, s->m_bg, s->v_bg, FF, s->lr_bg, s->beta1,
                                                              s->beta2, s->eps, (float)c1, (float)c2);
+    ++p->last_launches;
+  }
+  if (opt_delta) {
+    ptycho::k_adam<<<(int)((nD + 255) / 256), 256, 0, st>>>(p->d_delta, p->d_gdelta, s->m_delta, s->v_delta, nD,
+                                                             s->lr_delta, s->beta1, s->beta2, s->eps, (float)c1,
+                                                             (float)c2);
     ++p->last_launches;
   }
   if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;

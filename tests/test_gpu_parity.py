@@ -360,7 +360,7 @@ def test_pipeline_variants(dev, flags, F):
 
 def _sigma_bg_errors(case, plan, frames=None):
     batch = None if frames is None else torch.as_tensor(np.asarray(frames, np.int32), device=case.dev)
-    La, gO, gP, gs, gb = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
+    La, gO, gP, gs, gb, _ = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
     Lr, gsr, gbr = orc.gradient_sigma_bg(case.O0, case.P0, case.w.pos, case.Ih, case.loss, case.eps, case.sigma,
                                          case.bg, case.mask, case.taps, frames)
     _, gOr, gPr = case.oracle_grad(frames)
@@ -410,12 +410,12 @@ def test_sigma_gradient_without_sigma_and_at_zero(dev):
     w = syn.tiny_workload(F=64, L=1, M=2, n_side=3, step=10, seed=35, remap=False, loss="amplitude", with_bg=True)
     case = Case(w, dev, seed=2)
     plan = case.plan()
-    _, _, _, gs, _ = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    _, _, _, gs, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
     _, gsr, _ = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, None, case.bg)
     assert rel(gs.cpu().numpy(), gsr) < TOL_G
     sig = torch.ones(w.J, dtype=torch.float32, device=dev)
     sig[4] = 0.0
-    _, _, _, gs0, _ = plan.adjoint_ex(case.O, case.P, case.Im, sig, case.bg_t)
+    _, _, _, gs0, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, sig, case.bg_t)
     assert float(gs0[4].item()) == 0.0
     _, gsr0, _ = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps,
                                        sig.cpu().numpy().astype(np.float64), case.bg)
@@ -453,7 +453,7 @@ def test_step_updates_sigma_and_background(dev, device_counter):
     for it in range(2):
         x0 = dict(O=c128(O), P=c128(P), s=f64(sig), b=f64(bg))
         mom = {k: f64(getattr(st, k)) for k in ("mO", "vO", "mP", "vP", "m_sigma", "v_sigma", "m_bg", "v_bg")}
-        La, gO, gP, gs, gb = plan.adjoint_ex(O, P, case.Im, sig, bg, batch=bt)
+        La, gO, gP, gs, gb, _ = plan.adjoint_ex(O, P, case.Im, sig, bg, batch=bt)
         if it == 0:
             Lr, gsr, gbr = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, case.sigma,
                                                  case.bg, None, case.taps, frames)
@@ -504,4 +504,144 @@ def test_autograd_sigma_background(dev):
         Lm = float(ptycho_loss(case.O, case.P, plan, case.Im, sig - h * ds, bg - h * db).item())
     fd = (Lp - Lm) / (2 * h)
     assert abs(fd - an) < 2e-3 * abs(an), (fd, an)
+    plan.close()
+
+
+# ---------------------------------------------------------------------------------------
+# fractional scan offsets (f2 by the Fourier shift theorem) and the position gradient
+# ---------------------------------------------------------------------------------------
+
+def _offsets(w, seed, amp=0.5):
+    return np.random.default_rng(seed).uniform(-amp, amp, size=(w.L, w.J, 2))
+
+
+def _offset_errors(case, plan, delta, frames=None):
+    """GPU forward, loss and every gradient with offsets registered, against the oracle."""
+    w = case.w
+    d32 = np.asarray(delta, np.float32).astype(np.float64)          # the values the GPU sees
+    dt = torch.as_tensor(np.asarray(delta, np.float32), device=case.dev).contiguous()
+    plan.set_offsets(dt)
+    batch = None if frames is None else torch.as_tensor(np.asarray(frames, np.int32), device=case.dev)
+    Ip = plan.forward(case.O, case.P, case.sig_t, case.bg_t).cpu().numpy()
+    Ir = orc.predict(case.O0, case.P0, w.pos, case.sigma, case.bg, case.taps, delta=d32)
+    La, gO, gP, gs, gb, gd = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
+    args = (case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps)
+    Lr, gOr, gPr = orc.gradient(*args, case.sigma, case.bg, case.mask, case.taps, frames, delta=d32)
+    _, gdr = orc.gradient_delta(*args, d32, case.sigma, case.bg, case.mask, case.taps, frames)
+    _, gsr, gbr = orc.gradient_sigma_bg(*args, case.sigma, case.bg, case.mask, case.taps, frames, delta=d32)
+    gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    return dict(I=rel(Ip, Ir), L=abs(float(La.item()) - Lr) / abs(Lr), gO=rel(gO.cpu().numpy(), gOr),
+                gP=rel(gP.cpu().numpy(), gPr), gd=rel(gd.cpu().numpy(), gdr), gs=rel(gs.cpu().numpy(), gsr),
+                gb=rel(gb.cpu().numpy(), gbr), gd_gpu=gd.cpu().numpy(), status=plan.status())
+
+
+def _assert_offsets_ok(e):
+    assert e["status"] == 0, e
+    assert e["I"] < TOL_I and e["L"] < TOL_L, e
+    for k in ("gO", "gP", "gd", "gs", "gb"):
+        assert e[k] < TOL_G, (k, e)
+
+
+@pytest.mark.parametrize("F", [64, 128, 256, 512])
+def test_offsets_all_frame_sizes(dev, F):
+    w = syn.tiny_workload(F=F, L=2, M=2, n_side=3, step=F // 8, seed=70 + F, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(F), mask_kind="shared", seed=F + 1)
+    plan = case.plan()
+    _assert_offsets_ok(_offset_errors(case, plan, _offsets(w, F)))
+    plan.close()
+
+
+@pytest.mark.parametrize("loss,remap", [("amplitude", False), ("poisson", False), ("amplitude", True)])
+def test_offsets_losses_and_geometry(dev, loss, remap):
+    w = syn.tiny_workload(F=64, L=3, M=2, n_side=3, step=10, seed=81, remap=remap, loss=loss, with_sigma=True,
+                          with_bg=True)
+    case = Case(w, dev, z=strong_z(64), mask_kind="frame", seed=12)
+    plan = case.plan()
+    _assert_offsets_ok(_offset_errors(case, plan, _offsets(w, 3, amp=0.9)))
+    plan.close()
+
+
+@pytest.mark.parametrize("F", [64, 256])
+def test_offsets_batches_overlap_and_subset(dev, F):
+    """Several position batches on overlapping streams and a position subset in any order: the
+    position gradient is 0 outside the subset."""
+    w = syn.tiny_workload(F=F, L=2, M=3, n_side=4, step=F // 8, seed=83, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(F), mask_kind="frame", seed=13)
+    plan = case.plan(scratch_bytes=2 * 6 * F * F * 8, overlap=3)
+    delta = _offsets(w, 5)
+    _assert_offsets_ok(_offset_errors(case, plan, delta))
+    frames = [12, 1, 7, 4, 15]
+    e = _offset_errors(case, plan, delta, frames)
+    _assert_offsets_ok(e)
+    outside = np.setdiff1d(np.arange(w.J), frames)
+    assert np.all(e["gd_gpu"][:, outside, :] == 0.0)
+    plan.close()
+
+
+def test_zero_offsets_match_integer_positions_and_clearing_restores_them(dev):
+    w = syn.tiny_workload(F=128, L=2, M=2, n_side=3, step=14, seed=85, remap=True, loss="poisson", with_bg=True)
+    case = Case(w, dev, z=strong_z(128), seed=14)
+    plan = case.plan()
+    L0, gO0, gP0 = plan.adjoint(case.O, case.P, case.Im, None, case.bg_t)
+    plan.set_offsets(torch.zeros(w.L, w.J, 2, dtype=torch.float32, device=dev))
+    L1, gO1, gP1, _, _, gd1 = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    assert abs(float(L1.item()) - float(L0.item())) < 1e-6 * abs(float(L0.item()))
+    assert rel(gO1.cpu().numpy(), gO0.cpu().numpy()) < 1e-5 and rel(gP1.cpu().numpy(), gP0.cpu().numpy()) < 1e-5
+    _, gdr = orc.gradient_delta(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, np.zeros((w.L, w.J, 2)),
+                                None, case.bg, None, case.taps)
+    assert rel(gd1.cpu().numpy(), gdr) < TOL_G
+    plan.set_offsets(None)
+    L2, gO2, _ = plan.adjoint(case.O, case.P, case.Im, None, case.bg_t)
+    assert torch.equal(L2, L0) and torch.equal(gO2, gO0)          # the integer path again, bit for bit
+    plan.close()
+
+
+def test_offsets_reject_what_they_cannot_do(dev):
+    from paper_2311_14780_gb300 import AdamState, PtychoError, _native
+    from paper_2311_14780_gb300.api import _ptr
+    w = syn.tiny_workload(F=64, L=1, M=2, n_side=3, step=10, seed=87, remap=False, loss="amplitude")
+    case = Case(w, dev, seed=15)
+    plan = case.plan()
+    gd = torch.empty(w.L, w.J, 2, dtype=torch.float32, device=dev)
+    gO = torch.empty(plan.numel_O, dtype=torch.complex64, device=dev)
+    gP = torch.empty_like(case.P)
+    rc = _native.lib().ptycho_adjoint_ex(plan.handle, _ptr(torch.view_as_real(case.O)), _ptr(torch.view_as_real(case.P)),
+                                         None, None, _ptr(case.Im), None, 0, None, 0, _ptr(torch.view_as_real(gO)),
+                                         _ptr(torch.view_as_real(gP)), None, None, _ptr(gd), None, None)
+    assert rc == -1                                               # a position gradient needs offsets
+    plan.set_offsets(torch.zeros(w.L, w.J, 2, dtype=torch.float32, device=dev))
+    with pytest.raises(PtychoError):
+        plan.plain_step(AdamState(plan, 1e-2, 1e-2), case.O.clone(), case.P.clone(), case.Im)
+    plan.close()
+
+
+def test_step_updates_offsets(dev):
+    """ptycho_step with lr_delta > 0 moves the registered offsets by Adam on the position
+    gradient (checked against the oracle's Adam on the same gradient and state); the object,
+    probe and offsets updates all come from one deterministic pass."""
+    from paper_2311_14780_gb300 import AdamState
+    w = syn.tiny_workload(F=64, L=2, M=2, n_side=3, step=10, seed=89, remap=True, loss="poisson", with_sigma=True)
+    case = Case(w, dev, z=strong_z(64), seed=16)
+    plan = case.plan()
+    delta = torch.as_tensor(_offsets(w, 9).astype(np.float32), device=dev).contiguous()
+    plan.set_offsets(delta)
+    st = AdamState(plan, 1e-2, 1e-1, lr_delta=5e-2)
+    O, P = case.O.clone(), case.P.clone()
+    hp = dict(b1=float(np.float32(0.9)), b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)))
+    for it in range(2):
+        d0 = delta.detach().cpu().numpy().astype(np.float64).reshape(-1)
+        m0 = st.m_delta.cpu().numpy().astype(np.float64)
+        v0 = st.v_delta.cpu().numpy().astype(np.float64)
+        La, _, _, _, _, gd = plan.adjoint_ex(O, P, case.Im, case.sig_t)
+        if it == 0:
+            _, gdr = orc.gradient_delta(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps,
+                                        d0.reshape(w.L, w.J, 2), case.sigma, None, None, case.taps)
+            assert rel(gd.cpu().numpy(), gdr) < TOL_G
+        L = float(plan.step(st, O, P, case.Im, case.sig_t).item())
+        assert L == float(La.item())
+        ref = orc.adam_update_real(d0, gd.cpu().numpy().astype(np.float64).reshape(-1), m0, v0, it + 1, 5e-2, **hp)
+        new = delta.detach().cpu().numpy().astype(np.float64).reshape(-1)
+        assert rel(new - d0, ref - d0) < 1e-5, it
     plan.close()
