@@ -42,7 +42,9 @@ the intensity-level form of the sigma gradient that Parseval's theorem gives, an
 identity between the sigma gradient and the probe gradient along P -> cP; for the
 fractional offsets: whole-pixel offsets as cyclic rolls, band-limited plane waves sampled
 at the shifted points, unitarity, composition, the adjoint identity, reduction to the
-integer model, and finite differences of the loss in the offsets, O and P).  The tilted-plane remap formula itself is a reading of the
+integer model, and finite differences of the loss in the offsets, O and P; for z: finite
+differences of the fractional model indices and of the loss with the remap rebuilt at z +- h,
+exactness for an intensity linear on the model grid, and zero rate at the specular pixel).  The tilted-plane remap formula itself is a reading of the
 cited geometry and is only partially pinned (identity limit, constants, adjointness,
 the paper's NA and pixel-ratio figures).
 """
@@ -169,6 +171,35 @@ def remap_taps(F: int, z: float, det_pixel: float, tilt_rad: float) -> RemapTaps
     wy = np.where(valid, yhat - i0, 0.0)
     wx = np.where(valid, xhat - j0, 0.0)
     return RemapTaps(valid, i0, j0, wy, wx, yhat, xhat, db, da)
+
+
+def remap_index_rates(F: int, z: float, det_pixel: float, tilt_rad: float):
+    """d yhat / dz and d xhat / dz of every camera pixel's fractional model index (the
+    propagation distance z is among the variables the paper optimises).  With
+    yhat = z b / (p cos(alpha)) + F/2 and xhat = z a / p + F/2 (see remap_taps):
+    d yhat/dz = (b + z db/dz) / (p cos(alpha)), db/dz = sin(alpha)/R - (Y cos(alpha) + z sin(alpha)) z / R^3,
+    d xhat/dz = (X / p) (1/R - z^2 / R^3)."""
+    c, s = math.cos(tilt_rad), math.sin(tilt_rad)
+    y, x = np.mgrid[0:F, 0:F].astype(np.float64)
+    X = (x - F / 2) * det_pixel
+    Y = (y - F / 2) * det_pixel
+    R = np.sqrt(X * X + Y * Y + z * z)
+    b = (Y * c + z * s) / R - s
+    dbdz = s / R - (Y * c + z * s) * z / R ** 3
+    dy = (b + z * dbdz) / (det_pixel * c)
+    dx = (X / det_pixel) * (1.0 / R - z * z / R ** 3)
+    return dy, dx
+
+
+def remap_apply_rate(I_model: np.ndarray, taps: RemapTaps, rates) -> np.ndarray:
+    """d(R I)/dz at fixed model-grid I: the bilinear interpolant's slopes along the row and
+    column fractions times the index rates (0 where the pixel is invalid)."""
+    i, j, u, v, ok = taps.i0, taps.j0, taps.wy, taps.wx, taps.valid
+    I00, I01 = I_model[i, j], I_model[i, j + 1]
+    I10, I11 = I_model[i + 1, j], I_model[i + 1, j + 1]
+    d_row = ((1 - v) * I10 + v * I11) - ((1 - v) * I00 + v * I01)
+    d_col = (1 - u) * (I01 - I00) + u * (I11 - I10)
+    return np.where(ok, d_row * rates[0] + d_col * rates[1], 0.0)
 
 
 def _tap_weights(taps: RemapTaps):
@@ -408,6 +439,30 @@ def gradient_sigma_bg(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=Non
                 chi = f4_adjoint(2.0 * G * Psi[l, m])
                 g_sigma[j] += float(np.real(np.conj(P[l, m] * patches[l]) * chi).sum())
     return total, g_sigma, g_bg
+
+
+def gradient_z(O, P, pos, Imeas, kind, eps, taps, rates, sigma=None, bg=None, mask=None, frames=None, delta=None):
+    """Loss and dL/dz through the tilted-plane remap (the propagator itself is the
+    orthonormal DFT, with no z in it; a caller holding physical scan positions adds the
+    chain through the object pixel size, sum_j g_delta . d pos / dz).  For each frame,
+    dL/dz = sum over the camera grid of (mask dL/dI) * d(R (sum |Psi|^2 + N))/dz; the mask
+    boundary (pixels whose taps leave the grid) has measure zero and is held fixed."""
+    F = P.shape[2]
+    J = pos.shape[1]
+    frames = range(J) if frames is None else frames
+    total, gz = 0.0, 0.0
+    for j in frames:
+        _, Psi = frame_fields(O, P, pos, j, sigma, delta)
+        I_model = (np.abs(Psi) ** 2).sum(axis=(0, 1))
+        if bg is not None:
+            I_model = I_model + bg
+        Ic = remap_apply(I_model, taps)
+        mk = frame_mask(mask, j, F, taps)
+        total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
+        with np.errstate(divide="ignore", invalid="ignore"):
+            D = np.where(mk, loss_derivative(Ic, Imeas[j], kind, eps), 0.0)
+        gz += float((D * remap_apply_rate(I_model, taps, rates)).sum())
+    return total, gz
 
 
 # ----------------------------------------------------------------------------

@@ -590,3 +590,47 @@ def test_position_gradient_vanishes_at_noiseless_truth_and_for_frames_not_reques
     _, gd2 = orc.gradient_delta(w.O0, w.P0, w.pos, Ih2, "poisson", 1e-3, delta, w.sigma, w.bg, None, taps,
                                 frames=[1, 4])
     assert np.all(gd2[:, [0, 2, 3, 5, 6, 7, 8], :] == 0.0) and np.abs(gd2[:, [1, 4], :]).max() > 0
+
+
+# ----------------------------------------------------------------------------
+# propagation distance z (through the tilted-plane remap)
+# ----------------------------------------------------------------------------
+
+def test_remap_index_rates_match_finite_differences_and_vanish_at_the_specular_pixel():
+    F, z, p, al = 32, 4e-3, 15e-6, math.radians(70)
+    dy, dx = orc.remap_index_rates(F, z, p, al)
+    h = 1e-7 * z
+    tp, tm = orc.remap_taps(F, z + h, p, al), orc.remap_taps(F, z - h, p, al)
+    assert rel(dy, (tp.yhat - tm.yhat) / (2 * h)) < 1e-6 and rel(dx, (tp.xhat - tm.xhat) / (2 * h)) < 1e-6
+    assert abs(dy[F // 2, F // 2]) < 1e-12 * np.abs(dy).max() and dx[F // 2, F // 2] == 0.0
+
+
+def test_remap_rate_is_exact_for_an_intensity_linear_on_the_model_grid():
+    """Bilinear interpolation reproduces a linear function, so R I = al*yhat + be*xhat + c on
+    valid pixels and d(R I)/dz = al*dyhat/dz + be*dxhat/dz there."""
+    F, z, p, al = 32, 4e-3, 15e-6, math.radians(70)
+    taps = orc.remap_taps(F, z, p, al)
+    rates = orc.remap_index_rates(F, z, p, al)
+    r, c = np.mgrid[0:F, 0:F].astype(np.float64)
+    I = 0.7 * r - 0.3 * c + 5.0
+    got = orc.remap_apply_rate(I, taps, rates)
+    want = np.where(taps.valid, 0.7 * rates[0] - 0.3 * rates[1], 0.0)
+    assert rel(got, want) < 1e-12
+
+
+@pytest.mark.parametrize("kind", orc.LOSS_KINDS)
+def test_z_gradient_matches_central_finite_differences(kind):
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=61, remap=True, loss=kind, with_sigma=True, with_bg=True)
+    p, al = 15e-6, math.radians(70)
+    z = 2e-3
+    taps = orc.remap_taps(w.F, z, p, al)
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps), 9)
+    L0, gz = orc.gradient_z(w.O0, w.P0, w.pos, Ih, kind, 1e-3, taps, orc.remap_index_rates(w.F, z, p, al), w.sigma,
+                            w.bg)
+    assert abs(L0 - orc.loss(w.O0, w.P0, w.pos, Ih, kind, 1e-3, w.sigma, w.bg, None, taps)) <= 1e-13 * abs(L0)
+    h = 1e-9 * z
+    tp, tm = orc.remap_taps(w.F, z + h, p, al), orc.remap_taps(w.F, z - h, p, al)
+    assert np.array_equal(tp.valid, tm.valid) and np.array_equal(tp.i0, tm.i0) and np.array_equal(tp.j0, tm.j0)
+    fd = (orc.loss(w.O0, w.P0, w.pos, Ih, kind, 1e-3, w.sigma, w.bg, None, tp) -
+          orc.loss(w.O0, w.P0, w.pos, Ih, kind, 1e-3, w.sigma, w.bg, None, tm)) / (2 * h)
+    assert abs(fd - gz) <= 1e-5 * abs(gz) + 50 * 2.2e-16 * abs(L0) / h, (fd, gz)
