@@ -207,11 +207,28 @@ int ptycho_adjoint(ptycho_plan_t* plan, const float* O, const float* P, const fl
  *           domain: (1/F^2) Re sum_k conj(Ghat(k)) 2 pi i f(k) Q(k), Ghat the DFT of the
  *           gradient with respect to the shifted patch, Q the ramp times the DFT of the
  *           integer window, f in cycles per pixel.
+ *   g_z     [1] (device, FP64) OVERWRITTEN: dL/dz, the derivative with respect to the
+ *           propagation distance (a variable the paper optimises) at fixed object pixels and
+ *           positions.  The propagator here is the orthonormal DFT, so z enters through the
+ *           tilted-plane remap: dL/dz = sum over the call's frames and camera pixels of
+ *           (mask dL/dI) * (s_row drow/dz + s_col dcol/dz), s the slopes of the bilinear
+ *           interpolant of the model intensity (field + background) and (row, col) the
+ *           pixel's fractional model-grid index; pixels whose taps leave the grid are held
+ *           masked.  A caller with physical scan positions adds the chain through the object
+ *           pixel size lambda z / (F p): sum over (l, j) of g_delta . d pos / dz.  Requires
+ *           the remap (PTYCHO_EINVAL otherwise).
  * Other arguments as for ptycho_adjoint. */
 int ptycho_adjoint_ex(ptycho_plan_t* plan, const float* O, const float* P, const float* sigma,
                       const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
                       const int32_t* batch_idx, int nbatch, float* gO, float* gP, float* g_sigma,
-                      float* g_bg, float* g_delta, double* loss_dev, void* stream);
+                      float* g_bg, float* g_delta, double* g_z, double* loss_dev, void* stream);
+
+/* Moves the camera to distance z (> 0, metres): rebuilds the plan's tilted-plane remap (taps,
+ * their z rates and the transpose), for z correction driven by g_z.  Waits for the device
+ * to be idle first (no call of this plan may be in flight) and is synchronous; may
+ * reallocate the transpose's arrays.  PTYCHO_EUNSUPPORTED without the remap, PTYCHO_EINVAL
+ * for z <= 0; on failure the previous geometry is kept. */
+int ptycho_plan_set_distance(ptycho_plan_t* plan, double z);
 
 /* Fractional scan offsets (f2 by the Fourier shift theorem, the paper's differentiable
  * scanning shift; Section "Benchmarking with state-of-art ...").  Registers delta, a DEVICE

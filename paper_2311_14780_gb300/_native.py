@@ -61,7 +61,9 @@ SIGNATURES = [
     ("ptycho_forward", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ptycho_loss", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     ("ptycho_adjoint", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP]),
-    ("ptycho_adjoint_ex", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ptycho_adjoint_ex", _I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                               _VP]),
+    ("ptycho_plan_set_distance", _I, [_VP, ctypes.c_double]),
     ("ptycho_plan_set_offsets", _I, [_VP, _VP]),
     ("ptycho_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     ("ptycho_plan_status", _I, [_VP, c_int32_p]),

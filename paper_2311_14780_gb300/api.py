@@ -94,6 +94,7 @@ class Plan:
                  tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0, overlap: int = 0,
                  flags: int = 0, col_groups: int = 0):
         self.F, self.L, self.M, self.J = int(F), int(L), int(M), int(J)
+        self.remap = bool(remap)
         self.obj_shapes = [(int(h), int(w)) for (h, w) in obj_shapes]
         self.loss_kind = loss
         g, self._keep = geom_struct(F, L, M, J, obj_shapes, pos, loss=loss, eps=eps, remap=remap, z=z,
@@ -250,9 +251,14 @@ class Plan:
     def offsets(self):
         return getattr(self, "_delta", None)
 
-    def adjoint_ex(self, O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, stream=None):
+    def set_distance(self, z: float):
+        """ptycho_plan_set_distance: rebuild the tilted-plane remap for propagation distance z."""
+        _check(_native.lib().ptycho_plan_set_distance(self._h_plan, float(z)), "ptycho_plan_set_distance")
+
+    def adjoint_ex(self, O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, stream=None, want_z=None):
         """ptycho_adjoint_ex: (loss, grad O, grad P, grad sigma [J], grad bg [F, F],
-        grad delta [L, J, 2] or None when no offsets are registered)."""
+        grad delta [L, J, 2] or None when no offsets are registered, dL/dz [1] FP64 or None
+        without the remap; want_z=False skips it)."""
         FF = self.F * self.F
         Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
         m, mpf = self._mask(mask)
@@ -263,14 +269,16 @@ class Plan:
         gb = torch.empty(self.F, self.F, dtype=torch.float32, device=self.device)
         gd = torch.empty(self.L, self.J, 2, dtype=torch.float32, device=self.device) if self.offsets is not None \
             else None
+        want_z = self.remap if want_z is None else (want_z and self.remap)
+        gz = torch.zeros(1, dtype=torch.float64, device=self.device) if want_z else None
         loss_out = torch.zeros(1, dtype=torch.float64, device=self.device)
         rc = _native.lib().ptycho_adjoint_ex(self._h_plan, _ptr(Or), _ptr(Pr), _ptr(self._f32(sigma, self.J, "sigma")),
                                              _ptr(self._f32(bg, FF, "bg")),
                                              _ptr(self._f32(Imeas, self.J * FF, "Imeas")), _ptr(m), mpf, _ptr(bt), nb,
-                                             _ptr(gO), _ptr(gP), _ptr(gs), _ptr(gb), _ptr(gd), _ptr(loss_out),
+                                             _ptr(gO), _ptr(gP), _ptr(gs), _ptr(gb), _ptr(gd), _ptr(gz), _ptr(loss_out),
                                              _stream_handle(stream))
         _check(rc, "ptycho_adjoint_ex")
-        return loss_out, gO, gP, gs, gb, gd
+        return loss_out, gO, gP, gs, gb, gd, gz
 
     def step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, batch=None, loss_out=None,
              stream=None):

@@ -21,7 +21,8 @@ class PtychoLoss(torch.autograd.Function):
         s_d = None if sigma is None else sigma.detach()
         b_d = None if bg is None else bg.detach()
         if sb:
-            loss, gO, gP, gs, gb, _ = plan.adjoint_ex(O.detach(), P.detach(), Imeas, s_d, b_d, mask, batch)
+            loss, gO, gP, gs, gb, _, _ = plan.adjoint_ex(O.detach(), P.detach(), Imeas, s_d, b_d, mask, batch,
+                                                         want_z=False)
             ctx.save_for_backward(gO, gP, gs.reshape(sigma.shape) if sigma is not None else gs,
                                   gb.reshape(bg.shape) if bg is not None else gb)
         elif need[0] or need[1]:

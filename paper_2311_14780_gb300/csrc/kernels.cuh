@@ -380,6 +380,8 @@ struct LossArgs {
   float* I_pred;                 // [J][F][F] or null
   int remap;
   int Gsum;                      // intensity slices (mode groups) to add
+  const float2* tap_dz;          // [F*F] d(row, col index of the taps)/dz (remap only)
+  double* z_part;                // [nbatch][loss_blocks] sums of D * d(R I)/dz, or null
 };
 
 __device__ __forceinline__ float model_I(const float* Ip, const float* bg, int G, int FF, int u) {
@@ -409,24 +411,30 @@ __device__ __forceinline__ float poisson_term(float Ie, float Ih) {
 
 // Camera-grid prediction of one pixel q (remap: bilinear in the four model taps of q).
 // Is is the field part, Ib the background part; valid = false outside the remap's grid.
+// With the remap, srow / scol are the slopes of the bilinear interpolant of the full model
+// intensity (field + background) along the row and column fractions of the taps.
 template <int F>
 __device__ __forceinline__ void predict_pixel(const LossArgs& la, const float* Ip, int G, int q, int tb, float2 w,
-                                              float& Is, float& Ib, bool& valid) {
+                                              float& Is, float& Ib, bool& valid, float& srow, float& scol) {
   constexpr int FF = F * F;
   Is = 0.f;
   Ib = 0.f;
+  srow = scol = 0.f;
   valid = true;
   if (la.remap) {
     valid = tb >= 0;
     if (!valid) return;
-    const float i00 = model_I(Ip, nullptr, G, FF, tb), i01 = model_I(Ip, nullptr, G, FF, tb + 1);
-    const float i10 = model_I(Ip, nullptr, G, FF, tb + F), i11 = model_I(Ip, nullptr, G, FF, tb + F + 1);
+    float i00 = model_I(Ip, nullptr, G, FF, tb), i01 = model_I(Ip, nullptr, G, FF, tb + 1);
+    float i10 = model_I(Ip, nullptr, G, FF, tb + F), i11 = model_I(Ip, nullptr, G, FF, tb + F + 1);
     Is = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
     if (la.bg) {
       const float b00 = __ldg(la.bg + tb), b01 = __ldg(la.bg + tb + 1);
       const float b10 = __ldg(la.bg + tb + F), b11 = __ldg(la.bg + tb + F + 1);
       Ib = (1.f - w.x) * ((1.f - w.y) * b00 + w.y * b01) + w.x * ((1.f - w.y) * b10 + w.y * b11);
+      i00 += b00; i01 += b01; i10 += b10; i11 += b11;
     }
+    srow = ((1.f - w.y) * i10 + w.y * i11) - ((1.f - w.y) * i00 + w.y * i01);
+    scol = (1.f - w.x) * (i01 - i00) + w.x * (i11 - i10);
   } else {
     Is = model_I(Ip, nullptr, G, FF, q);
     if (la.bg) Ib = __ldg(la.bg + q);
@@ -473,7 +481,7 @@ k_loss(KArgs a, LossArgs la) {
   pdl_wait();
   pdl_trigger();
   constexpr int FF = F * F, NB = loss_blocks<F>();
-  __shared__ float red[4][kLossThreads / 32];
+  __shared__ float red[6][kLossThreads / 32];
   const int b = blockIdx.y;
   const int i = a.batch_off + b;
   const int q0 = (blockIdx.x * kLossThreads + threadIdx.x) * kLossPx;
@@ -481,6 +489,7 @@ k_loss(KArgs a, LossArgs la) {
   if (j < 0) {
     if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * NB + blockIdx.x] = 0.0;
     if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * NB + blockIdx.x] = 0.0;
+    if (la.z_part && threadIdx.x == 0) la.z_part[(long long)i * NB + blockIdx.x] = 0.0;
     if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
@@ -500,12 +509,13 @@ k_loss(KArgs a, LossArgs la) {
   }
   float d[kLossPx];
   float th = 0.f, tl = 0.f, sh = 0.f, sl = 0.f;   // double-float sums of the loss and sigma terms
+  float zh = 0.f, zl = 0.f;                       // and of the z terms
 #pragma unroll
   for (int k = 0; k < kLossPx; ++k) {
     const int q = q0 + k;
-    float Is, Ib;
+    float Is, Ib, srow, scol;
     bool valid;
-    predict_pixel<F>(la, Ip, la.Gsum, q, tb[k], tw[k], Is, Ib, valid);
+    predict_pixel<F>(la, Ip, la.Gsum, q, tb[k], tw[k], Is, Ib, valid, srow, scol);
     const float Ic = Is + Ib;
     if (la.I_pred) la.I_pred[(long long)j * FF + q] = valid ? Ic : 0.f;
     d[k] = 0.f;
@@ -525,24 +535,31 @@ k_loss(KArgs a, LossArgs la) {
         }
       }
       df_add(sh, sl, d[k] * Is);
+      if (la.z_part && d[k] != 0.f) {
+        const float2 rz = __ldg(la.tap_dz + q);
+        df_add(zh, zl, d[k] * fmaf(srow, rz.x, scol * rz.y));
+      }
     }
   }
   if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(d[0], d[1], d[2], d[3]);
-  if (!la.loss_part && !la.sig_part) return;
+  if (!la.loss_part && !la.sig_part && !la.z_part) return;
   df_warp_sum(th, tl);
   df_warp_sum(sh, sl);
+  df_warp_sum(zh, zl);
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = th;
     red[1][threadIdx.x >> 5] = tl;
     red[2][threadIdx.x >> 5] = sh;
     red[3][threadIdx.x >> 5] = sl;
+    red[4][threadIdx.x >> 5] = zh;
+    red[5][threadIdx.x >> 5] = zl;
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
+  if (threadIdx.x < 3) {
     double sum = 0.0;
     for (int wi = 0; wi < kLossThreads / 32; ++wi)
       sum += (double)red[2 * threadIdx.x][wi] + (double)red[2 * threadIdx.x + 1][wi];
-    double* out = threadIdx.x == 0 ? la.loss_part : la.sig_part;
+    double* out = threadIdx.x == 0 ? la.loss_part : (threadIdx.x == 1 ? la.sig_part : la.z_part);
     if (out) out[(long long)i * NB + blockIdx.x] = sum;
   }
 }

@@ -155,6 +155,8 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.I_pred = c.kind == CallKind::Forward ? c.I_pred : nullptr;
   la.remap = p.remap;
   la.Gsum = p.G;
+  la.tap_dz = p.d_tap_dz;
+  la.z_part = grad && c.g_z ? p.d_z_part : nullptr;
 
   AdjArgs aa{};
   aa.D = p.d_D;
@@ -337,6 +339,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   if (grad && nsplit > 1)
     PTY_LAUNCH(p, kRowAdj, st,
                launch_pdl(k_sum_splits, dim3(4 * p.sms), 256, 0, st, (const float2*)gPs, nsplit, p.P_numel, c.gP));
+  if (grad && c.g_z)
+    PTY_LAUNCH(p, kLossReduce, st,
+               launch_pdl(k_loss_reduce, 1, 256, 0, st, (const double*)p.d_z_part,
+                          (long long)c.nbatch * loss_blocks<F>(), c.g_z));
   if (grad && c.g_delta)
     PTY_LAUNCH(p, kShift, st,
                launch_pdl(k_delta_grad, dim3((p.L * p.J + 255) / 256), 256, 0, st, (const int32_t*)c.bidx, c.nbatch,

@@ -72,6 +72,11 @@ struct ptycho_plan {
   // fractional scan offsets (ptycho_plan_set_offsets): the caller's [L][J][2] array and the
   // per-set workspaces of the Fourier shift (allocated on first registration)
   float* d_delta = nullptr;
+  // remap geometry (rebuilt by ptycho_plan_set_distance) and the z-gradient workspace
+  double z = 0.0, det_pixel = 0.0, tilt_rad = 0.0;
+  float2* d_tap_dz = nullptr;                  // [F*F] d(row, col tap index)/dz
+  double* d_z_part = nullptr;                  // [J][loss_blocks] z-gradient partials
+  long long rt_cap = 0;                        // capacity of d_rt_idx / d_rt_w
   float2* d_shT = nullptr;                     // [nsets][B][L][F][F] transform workspace
   float2* d_shQ = nullptr;                     // [nsets][B][L][F][F] ramp * spectrum of the windows
   float2* d_shP = nullptr;                     // [nsets][B][L][F][F] shifted patches
@@ -113,6 +118,7 @@ struct CallArgs {
   float* g_sigma;          // [J] or null
   float* g_bg;             // [F][F] or null
   float* g_delta;          // [L][J][2] or null (requires registered offsets)
+  double* g_z;             // [1] dL/dz (device) or null (requires the remap)
   double* loss;
 };
 

@@ -181,6 +181,41 @@ int upload(T* dst, const T* src, long long count) {
                                                                                               : PTYCHO_ECUDA;
 }
 
+void build_remap(int F, double z, double p, double alpha, std::vector<int32_t>& base, std::vector<float2>& w,
+                 std::vector<int32_t>& rt_ptr, std::vector<int32_t>& rt_idx, std::vector<float>& rt_w,
+                 std::vector<float2>& dz);
+
+// (Re)builds the remap tables of p for p->z: taps, index rates and the CSR transpose, whose
+// index and weight arrays are reallocated to their new length.  Synchronous.
+int load_remap(ptycho_plan* p) {
+  const int F = p->F;
+  const long long FF = (long long)F * F;
+  std::vector<int32_t> base, rt_ptr, rt_idx;
+  std::vector<float2> w, dz;
+  std::vector<float> rt_w;
+  build_remap(F, p->z, p->det_pixel, p->tilt_rad, base, w, rt_ptr, rt_idx, rt_w, dz);
+  const long long n = std::max<long long>(1, (long long)rt_idx.size());
+  if (n > p->rt_cap) {
+    if (p->d_rt_idx) cudaFree(p->d_rt_idx);
+    if (p->d_rt_w) cudaFree(p->d_rt_w);
+    p->bytes -= p->rt_cap * (long long)(sizeof(int32_t) + sizeof(float));
+    p->d_rt_idx = nullptr;
+    p->d_rt_w = nullptr;
+    p->rt_cap = 0;
+    int rc = dalloc(p, &p->d_rt_idx, n);
+    rc = rc ? rc : dalloc(p, &p->d_rt_w, n);
+    if (rc) return rc;
+    p->rt_cap = n;
+  }
+  int rc = upload(p->d_tap_base, base.data(), FF);
+  rc = rc ? rc : upload(p->d_tap_w, w.data(), FF);
+  rc = rc ? rc : upload(p->d_tap_dz, dz.data(), FF);
+  rc = rc ? rc : upload(p->d_rt_ptr, rt_ptr.data(), FF + 1);
+  rc = rc ? rc : upload(p->d_rt_idx, rt_idx.data(), (long long)rt_idx.size());
+  rc = rc ? rc : upload(p->d_rt_w, rt_w.data(), (long long)rt_w.size());
+  return rc;
+}
+
 void free_plan(ptycho_plan* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -195,7 +230,7 @@ void free_plan(ptycho_plan* p) {
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
                   p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs, p->d_shT, p->d_shQ, p->d_shP,
-                  p->d_dpart, p->d_gdelta};
+                  p->d_dpart, p->d_gdelta, p->d_tap_dz, p->d_z_part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -209,13 +244,18 @@ void free_plan(ptycho_plan* p) {
 // (p/z) cos(alpha) and p/z around the specular direction.  Each camera pixel takes the
 // bilinear interpolation of its four surrounding model pixels; it is invalid (masked) when
 // they leave the grid.  Index decisions are taken in FP64.
+// Also dz: per camera pixel, the rates d(row index)/dz and d(column index)/dz of its
+// fractional model-grid position (row index = z b / (p cos alpha) + F/2, column index =
+// z a / p + F/2, a and b the direction cosines below), for the gradient with respect to z.
 void build_remap(int F, double z, double p, double alpha, std::vector<int32_t>& base, std::vector<float2>& w,
-                 std::vector<int32_t>& rt_ptr, std::vector<int32_t>& rt_idx, std::vector<float>& rt_w) {
+                 std::vector<int32_t>& rt_ptr, std::vector<int32_t>& rt_idx, std::vector<float>& rt_w,
+                 std::vector<float2>& dz) {
   const double c = cos(alpha), s = sin(alpha);
   const double da = p / z, db = da * c;
   const int FF = F * F;
   base.assign(FF, -1);
   w.assign(FF, make_float2(0.f, 0.f));
+  dz.assign(FF, make_float2(0.f, 0.f));
   std::vector<double> wy(FF, 0.0), wx(FF, 0.0);
   for (int y = 0; y < F; ++y) {
     for (int x = 0; x < F; ++x) {
@@ -232,6 +272,9 @@ void build_remap(int F, double z, double p, double alpha, std::vector<int32_t>& 
         wy[y * F + x] = yh - iy;
         wx[y * F + x] = xh - ix;
         w[y * F + x] = make_float2((float)(yh - iy), (float)(xh - ix));
+        const double R3 = R * R * R;
+        const double b_z = s / R - (Y * c + z * s) * z / R3;
+        dz[y * F + x] = make_float2((float)((b + z * b_z) / (p * c)), (float)((X / p) * (1.0 / R - z * z / R3)));
       }
     }
   }
@@ -538,21 +581,16 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   rc = rc ? rc : upload(p->d_ident, ident.data(), g->J);
   rc = rc ? rc : upload(p->d_tw, tw.data(), (long long)tw.size());
   if (!rc && p->remap) {
-    std::vector<int32_t> base, rt_ptr, rt_idx;
-    std::vector<float2> w;
-    std::vector<float> rt_w;
-    build_remap(F, g->z, g->det_pixel, g->tilt_rad, base, w, rt_ptr, rt_idx, rt_w);
-    rc = rc ? rc : dalloc(p, &p->d_Gt, (long long)p->nsets * p->B * FF);
+    p->z = g->z;
+    p->det_pixel = g->det_pixel;
+    p->tilt_rad = g->tilt_rad;
+    rc = dalloc(p, &p->d_Gt, (long long)p->nsets * p->B * FF);
     rc = rc ? rc : dalloc(p, &p->d_tap_base, FF);
     rc = rc ? rc : dalloc(p, &p->d_tap_w, FF);
+    rc = rc ? rc : dalloc(p, &p->d_tap_dz, FF);
     rc = rc ? rc : dalloc(p, &p->d_rt_ptr, FF + 1);
-    rc = rc ? rc : dalloc(p, &p->d_rt_idx, std::max<long long>(1, (long long)rt_idx.size()));
-    rc = rc ? rc : dalloc(p, &p->d_rt_w, std::max<long long>(1, (long long)rt_w.size()));
-    rc = rc ? rc : upload(p->d_tap_base, base.data(), FF);
-    rc = rc ? rc : upload(p->d_tap_w, w.data(), FF);
-    rc = rc ? rc : upload(p->d_rt_ptr, rt_ptr.data(), FF + 1);
-    rc = rc ? rc : upload(p->d_rt_idx, rt_idx.data(), (long long)rt_idx.size());
-    rc = rc ? rc : upload(p->d_rt_w, rt_w.data(), (long long)rt_w.size());
+    rc = rc ? rc : dalloc(p, &p->d_z_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
+    rc = rc ? rc : load_remap(p);
   }
   if (rc) { free_plan(p); return rc; }
   *out = p;
@@ -627,6 +665,23 @@ int ptycho_forward(ptycho_plan_t* p, const float* O, const float* P, const float
   return dispatch(p, c, (cudaStream_t)stream);
 }
 
+int ptycho_plan_set_distance(ptycho_plan_t* p, double z) {
+  if (!p) return PTYCHO_EINVAL;
+  if (!p->remap) return PTYCHO_EUNSUPPORTED;
+  if (!(z > 0.0) || !isfinite(z)) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PTYCHO_ECUDA;   // no call of this plan in flight
+  const double old = p->z;
+  p->z = z;
+  rc = load_remap(p);
+  if (rc) {
+    p->z = old;
+    load_remap(p);
+  }
+  return rc;
+}
+
 int ptycho_plan_set_offsets(ptycho_plan_t* p, float* delta) {
   if (!p) return PTYCHO_EINVAL;
   int rc = check_device(p);
@@ -689,15 +744,16 @@ int ptycho_adjoint(ptycho_plan_t* p, const float* O, const float* P, const float
                    const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
                    int nbatch, float* gO, float* gP, double* loss_dev, void* stream) {
   return ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch, gO, gP, nullptr,
-                           nullptr, nullptr, loss_dev, stream);
+                           nullptr, nullptr, nullptr, loss_dev, stream);
 }
 
 int ptycho_adjoint_ex(ptycho_plan_t* p, const float* O, const float* P, const float* sigma, const float* bg,
                       const float* I_meas, const uint8_t* mask, int mask_per_frame, const int32_t* batch_idx,
                       int nbatch, float* gO, float* gP, float* g_sigma, float* g_bg, float* g_delta,
-                      double* loss_dev, void* stream) {
+                      double* g_z, double* loss_dev, void* stream) {
   if (!p || !O || !P || !I_meas || !gO || !gP) return PTYCHO_EINVAL;
   if (g_delta && !p->d_delta) return PTYCHO_EINVAL;   // a position gradient needs registered offsets
+  if (g_z && !p->remap) return PTYCHO_EINVAL;         // z enters through the remap only
   int rc = check_device(p);
   if (rc) return rc;
   CallArgs c{};
@@ -714,6 +770,7 @@ int ptycho_adjoint_ex(ptycho_plan_t* p, const float* O, const float* P, const fl
   c.g_sigma = g_sigma;
   c.g_bg = g_bg;
   c.g_delta = g_delta;
+  c.g_z = g_z;
   c.loss = loss_dev;
   rc = fill_batch(p, c, batch_idx, nbatch);
   if (rc) return rc;
@@ -732,7 +789,7 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
   int rc = ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
                              reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP),
                              opt_sigma ? p->d_gsig : nullptr, opt_bg ? p->d_gbg : nullptr,
-                             opt_delta ? p->d_gdelta : nullptr, loss_dev, stream);
+                             opt_delta ? p->d_gdelta : nullptr, nullptr, loss_dev, stream);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;

@@ -360,7 +360,7 @@ def test_pipeline_variants(dev, flags, F):
 
 def _sigma_bg_errors(case, plan, frames=None):
     batch = None if frames is None else torch.as_tensor(np.asarray(frames, np.int32), device=case.dev)
-    La, gO, gP, gs, gb, _ = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
+    La, gO, gP, gs, gb, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
     Lr, gsr, gbr = orc.gradient_sigma_bg(case.O0, case.P0, case.w.pos, case.Ih, case.loss, case.eps, case.sigma,
                                          case.bg, case.mask, case.taps, frames)
     _, gOr, gPr = case.oracle_grad(frames)
@@ -410,12 +410,12 @@ def test_sigma_gradient_without_sigma_and_at_zero(dev):
     w = syn.tiny_workload(F=64, L=1, M=2, n_side=3, step=10, seed=35, remap=False, loss="amplitude", with_bg=True)
     case = Case(w, dev, seed=2)
     plan = case.plan()
-    _, _, _, gs, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    _, _, _, gs, _, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
     _, gsr, _ = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, None, case.bg)
     assert rel(gs.cpu().numpy(), gsr) < TOL_G
     sig = torch.ones(w.J, dtype=torch.float32, device=dev)
     sig[4] = 0.0
-    _, _, _, gs0, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, sig, case.bg_t)
+    _, _, _, gs0, _, _, _ = plan.adjoint_ex(case.O, case.P, case.Im, sig, case.bg_t)
     assert float(gs0[4].item()) == 0.0
     _, gsr0, _ = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps,
                                        sig.cpu().numpy().astype(np.float64), case.bg)
@@ -453,7 +453,7 @@ def test_step_updates_sigma_and_background(dev, device_counter):
     for it in range(2):
         x0 = dict(O=c128(O), P=c128(P), s=f64(sig), b=f64(bg))
         mom = {k: f64(getattr(st, k)) for k in ("mO", "vO", "mP", "vP", "m_sigma", "v_sigma", "m_bg", "v_bg")}
-        La, gO, gP, gs, gb, _ = plan.adjoint_ex(O, P, case.Im, sig, bg, batch=bt)
+        La, gO, gP, gs, gb, _, _ = plan.adjoint_ex(O, P, case.Im, sig, bg, batch=bt)
         if it == 0:
             Lr, gsr, gbr = orc.gradient_sigma_bg(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, case.sigma,
                                                  case.bg, None, case.taps, frames)
@@ -524,7 +524,7 @@ def _offset_errors(case, plan, delta, frames=None):
     batch = None if frames is None else torch.as_tensor(np.asarray(frames, np.int32), device=case.dev)
     Ip = plan.forward(case.O, case.P, case.sig_t, case.bg_t).cpu().numpy()
     Ir = orc.predict(case.O0, case.P0, w.pos, case.sigma, case.bg, case.taps, delta=d32)
-    La, gO, gP, gs, gb, gd = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
+    La, gO, gP, gs, gb, gd, _ = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
     args = (case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps)
     Lr, gOr, gPr = orc.gradient(*args, case.sigma, case.bg, case.mask, case.taps, frames, delta=d32)
     _, gdr = orc.gradient_delta(*args, d32, case.sigma, case.bg, case.mask, case.taps, frames)
@@ -586,7 +586,7 @@ def test_zero_offsets_match_integer_positions_and_clearing_restores_them(dev):
     plan = case.plan()
     L0, gO0, gP0 = plan.adjoint(case.O, case.P, case.Im, None, case.bg_t)
     plan.set_offsets(torch.zeros(w.L, w.J, 2, dtype=torch.float32, device=dev))
-    L1, gO1, gP1, _, _, gd1 = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    L1, gO1, gP1, _, _, gd1, _ = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
     assert abs(float(L1.item()) - float(L0.item())) < 1e-6 * abs(float(L0.item()))
     assert rel(gO1.cpu().numpy(), gO0.cpu().numpy()) < 1e-5 and rel(gP1.cpu().numpy(), gP0.cpu().numpy()) < 1e-5
     _, gdr = orc.gradient_delta(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, np.zeros((w.L, w.J, 2)),
@@ -609,7 +609,7 @@ def test_offsets_reject_what_they_cannot_do(dev):
     gP = torch.empty_like(case.P)
     rc = _native.lib().ptycho_adjoint_ex(plan.handle, _ptr(torch.view_as_real(case.O)), _ptr(torch.view_as_real(case.P)),
                                          None, None, _ptr(case.Im), None, 0, None, 0, _ptr(torch.view_as_real(gO)),
-                                         _ptr(torch.view_as_real(gP)), None, None, _ptr(gd), None, None)
+                                         _ptr(torch.view_as_real(gP)), None, None, _ptr(gd), None, None, None)
     assert rc == -1                                               # a position gradient needs offsets
     plan.set_offsets(torch.zeros(w.L, w.J, 2, dtype=torch.float32, device=dev))
     with pytest.raises(PtychoError):
@@ -634,7 +634,7 @@ def test_step_updates_offsets(dev):
         d0 = delta.detach().cpu().numpy().astype(np.float64).reshape(-1)
         m0 = st.m_delta.cpu().numpy().astype(np.float64)
         v0 = st.v_delta.cpu().numpy().astype(np.float64)
-        La, _, _, _, _, gd = plan.adjoint_ex(O, P, case.Im, case.sig_t)
+        La, _, _, _, _, gd, _ = plan.adjoint_ex(O, P, case.Im, case.sig_t)
         if it == 0:
             _, gdr = orc.gradient_delta(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps,
                                         d0.reshape(w.L, w.J, 2), case.sigma, None, None, case.taps)
@@ -645,3 +645,77 @@ def test_step_updates_offsets(dev):
         new = delta.detach().cpu().numpy().astype(np.float64).reshape(-1)
         assert rel(new - d0, ref - d0) < 1e-5, it
     plan.close()
+
+
+# ---------------------------------------------------------------------------------------
+# propagation distance z (through the tilted-plane remap)
+# ---------------------------------------------------------------------------------------
+
+def _z_errors(case, plan, frames=None, delta=None):
+    w = case.w
+    batch = None if frames is None else torch.as_tensor(np.asarray(frames, np.int32), device=case.dev)
+    La, _, _, _, _, _, gz = plan.adjoint_ex(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
+    rates = orc.remap_index_rates(w.F, case.z, w.geom.det_pixel, w.geom.tilt_rad)
+    Lr, gzr = orc.gradient_z(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, case.taps, rates, case.sigma,
+                             case.bg, case.mask, frames, delta)
+    return abs(float(La.item()) - Lr) / abs(Lr), abs(float(gz.item()) - gzr) / abs(gzr)
+
+
+@pytest.mark.parametrize("F,loss,mask_kind", [(64, "poisson", "frame"), (64, "amplitude", None),
+                                              (256, "poisson", "shared"), (512, "amplitude", None)])
+def test_z_gradient(dev, F, loss, mask_kind):
+    w = syn.tiny_workload(F=F, L=2, M=2, n_side=3, step=F // 8, seed=91 + F, remap=True, loss=loss, with_sigma=True,
+                          with_bg=True)
+    case = Case(w, dev, z=strong_z(F), mask_kind=mask_kind, seed=17)
+    plan = case.plan(scratch_bytes=2 * 4 * F * F * 8)                      # several batches
+    eL, ez = _z_errors(case, plan)
+    assert eL < TOL_L and ez < TOL_G, (eL, ez)
+    eL, ez = _z_errors(case, plan, frames=[5, 0, 7])
+    assert eL < TOL_L and ez < TOL_G, (eL, ez)
+    plan.close()
+
+
+def test_z_gradient_with_offsets(dev):
+    w = syn.tiny_workload(F=64, L=2, M=2, n_side=3, step=8, seed=95, remap=True, loss="poisson", with_bg=True)
+    case = Case(w, dev, z=strong_z(64), seed=18)
+    plan = case.plan()
+    delta = np.random.default_rng(3).uniform(-0.5, 0.5, size=(w.L, w.J, 2)).astype(np.float32)
+    plan.set_offsets(torch.as_tensor(delta, device=dev))
+    eL, ez = _z_errors(case, plan, delta=delta.astype(np.float64))
+    assert eL < TOL_L and ez < TOL_G, (eL, ez)
+    plan.close()
+
+
+def test_set_distance_rebuilds_the_remap(dev):
+    """After ptycho_plan_set_distance(z2) the model is the oracle's at z2; going back to z gives
+    the first results bit for bit; the remap-free plan refuses both z calls."""
+    from paper_2311_14780_gb300 import PtychoError
+    w = syn.tiny_workload(F=128, L=2, M=2, n_side=3, step=14, seed=97, remap=True, loss="poisson", with_bg=True)
+    z1 = strong_z(128)
+    case = Case(w, dev, z=z1, seed=19)
+    plan = case.plan()
+    I1 = plan.forward(case.O, case.P, None, case.bg_t).clone()
+    g1 = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    z2 = 1.3 * z1
+    plan.set_distance(z2)
+    taps2 = orc.remap_taps(w.F, z2, w.geom.det_pixel, w.geom.tilt_rad)
+    I2 = plan.forward(case.O, case.P, None, case.bg_t).cpu().numpy()
+    assert rel(I2, orc.predict(case.O0, case.P0, w.pos, None, case.bg, taps2)) < TOL_I
+    _, _, _, _, _, _, gz2 = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    _, gzr = orc.gradient_z(case.O0, case.P0, w.pos, case.Ih, case.loss, case.eps, taps2,
+                            orc.remap_index_rates(w.F, z2, w.geom.det_pixel, w.geom.tilt_rad), None, case.bg)
+    assert abs(float(gz2.item()) - gzr) < TOL_G * abs(gzr)
+    plan.set_distance(z1)
+    assert torch.equal(plan.forward(case.O, case.P, None, case.bg_t), I1)
+    g1b = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    assert torch.equal(g1b[0], g1[0]) and torch.equal(g1b[1], g1[1]) and torch.equal(g1b[6], g1[6])
+    with pytest.raises(PtychoError):
+        plan.set_distance(-1.0)
+    plan.close()
+    w0 = syn.tiny_workload(F=64, L=1, M=1, n_side=2, step=8, seed=98, remap=False)
+    c0 = Case(w0, dev, seed=20)
+    p0 = c0.plan()
+    with pytest.raises(PtychoError):
+        p0.set_distance(0.1)
+    assert p0.adjoint_ex(c0.O, c0.P, c0.Im)[6] is None
+    p0.close()
