@@ -401,6 +401,24 @@ def run_ours(args, rank: int, world: int):
         pos_ms = timed(lambda: plan.step(st_pos, O2, P2, Im, loss_out=loss), args.corrections_steps)
         st_all = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2, lr_sigma=1e-2, lr_bg=1e-2)
         all_ms = timed(lambda: plan.step(st_all, O2, P2, Im, sig, bgt, loss_out=loss), args.corrections_steps)
+        z_ms = None
+        if w.geom.remap:
+            # + dL/dz from the same pass, then a host Adam step on z and the remap rebuilt for it
+            st_z = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2, lr_sigma=1e-2, lr_bg=1e-2,
+                             with_z_gradient=True)
+            zs = {"z": float(w.geom.z), "m": 0.0, "v": 0.0, "t": 0}
+
+            def z_step():
+                plan.step(st_z, O2, P2, Im, sig, bgt, loss_out=loss)
+                g = float(st_z.g_z.item())
+                zs["t"] += 1
+                zs["m"] = 0.9 * zs["m"] + 0.1 * g
+                zs["v"] = 0.999 * zs["v"] + 0.001 * g * g
+                mh, vh = zs["m"] / (1 - 0.9 ** zs["t"]), zs["v"] / (1 - 0.999 ** zs["t"])
+                zs["z"] -= 1e-7 * mh / (math.sqrt(vh) + 1e-12)
+                plan.set_distance(zs["z"])
+            z_ms = timed(z_step, args.corrections_steps)
+            plan.set_distance(float(w.geom.z))
         plan.set_offsets(None)
         corrections = {
             "steps": args.corrections_steps,
@@ -409,6 +427,9 @@ def run_ours(args, rank: int, world: int):
                                "relative_time": pos_ms / base_ms},
             "plus_positions_power_background": {"ms_per_step": all_ms, "evals_per_s": evals / (all_ms / 1e3),
                                                 "relative_time": all_ms / base_ms},
+            "plus_positions_power_background_distance": None if z_ms is None else
+            {"ms_per_step": z_ms, "evals_per_s": evals / (z_ms / 1e3), "relative_time": z_ms / base_ms,
+             "note": "dL/dz in the same pass; z updated by Adam on the host and the remap rebuilt every step"},
             "note": "fractional scan offsets (Fourier shift) optimised by Adam in the same step; uniform(-0.5, 0.5) px"}
 
     cpu = None

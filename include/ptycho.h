@@ -144,6 +144,10 @@ typedef struct {
    * optimised too (the paper refines the scan positions s_k with the other variables). */
   float lr_delta;                   /* > 0: ptycho_step updates the offsets in place          */
   float* m_delta; float* v_delta;   /* [L*J*2], required when lr_delta > 0                    */
+  /* Optional: non-NULL (device, 1 double) makes ptycho_step also write dL/dz of its pass
+   * (see g_z of ptycho_adjoint_ex; requires the remap).  z itself lives in the plan's host
+   * geometry: the caller updates it with ptycho_plan_set_distance. */
+  double* g_z;
 } ptycho_adam_t;
 
 /* Validates the geometry and every scan position (PTYCHO_ERANGE names an out-of-object

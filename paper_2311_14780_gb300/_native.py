@@ -36,6 +36,7 @@ class Adam(ctypes.Structure):
         ("m_sigma", ctypes.c_void_p), ("v_sigma", ctypes.c_void_p), ("m_bg", ctypes.c_void_p),
         ("v_bg", ctypes.c_void_p),
         ("lr_delta", ctypes.c_float), ("m_delta", ctypes.c_void_p), ("v_delta", ctypes.c_void_p),
+        ("g_z", ctypes.c_void_p),
     ]
 
 

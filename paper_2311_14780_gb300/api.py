@@ -322,7 +322,7 @@ class AdamState:
 
     def __init__(self, plan: Plan, lr_O: float, lr_P: float, beta1: float = 0.9, beta2: float = 0.999,
                  eps: float = 1e-8, device_counter: bool = False, lr_sigma: float = 0.0, lr_bg: float = 0.0,
-                 lr_delta: float = 0.0):
+                 lr_delta: float = 0.0, with_z_gradient: bool = False):
         dev = plan.device
         # optional: sigma [J] and the background [F, F] are optimised too (updated in place by
         # Plan.step, which then needs them as float32 device tensors)
@@ -335,6 +335,8 @@ class AdamState:
         self.lr_delta = lr_delta
         self.m_delta = torch.zeros(plan.L * plan.J * 2, dtype=torch.float32, device=dev) if lr_delta > 0 else None
         self.v_delta = torch.zeros_like(self.m_delta) if lr_delta > 0 else None
+        # optional: each step also writes dL/dz here (FP64, device); z is updated by the caller
+        self.g_z = torch.zeros(1, dtype=torch.float64, device=dev) if with_z_gradient else None
         # with a device step counter a captured CUDA graph of Plan.step can be replayed
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=dev) if device_counter else None
         self.lr_O, self.lr_P, self.beta1, self.beta2, self.eps = lr_O, lr_P, beta1, beta2, eps
@@ -351,7 +353,7 @@ class AdamState:
         s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
         s.t_dev = None if self.t_dev is None else self.t_dev.data_ptr()
         s.lr_sigma, s.lr_bg, s.lr_delta = self.lr_sigma, self.lr_bg, self.lr_delta
-        for name in ("m_sigma", "v_sigma", "m_bg", "v_bg", "m_delta", "v_delta"):
+        for name in ("m_sigma", "v_sigma", "m_bg", "v_bg", "m_delta", "v_delta", "g_z"):
             t = getattr(self, name)
             setattr(s, name, None if t is None else t.data_ptr())
         return s

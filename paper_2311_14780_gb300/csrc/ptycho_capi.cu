@@ -789,7 +789,7 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
   int rc = ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
                              reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP),
                              opt_sigma ? p->d_gsig : nullptr, opt_bg ? p->d_gbg : nullptr,
-                             opt_delta ? p->d_gdelta : nullptr, nullptr, loss_dev, stream);
+                             opt_delta ? p->d_gdelta : nullptr, s->g_z, loss_dev, stream);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;

@@ -719,3 +719,15 @@ def test_set_distance_rebuilds_the_remap(dev):
         p0.set_distance(0.1)
     assert p0.adjoint_ex(c0.O, c0.P, c0.Im)[6] is None
     p0.close()
+
+
+def test_step_writes_the_z_gradient_of_its_pass(dev):
+    from paper_2311_14780_gb300 import AdamState
+    w = syn.tiny_workload(F=64, L=2, M=2, n_side=3, step=8, seed=99, remap=True, loss="poisson", with_bg=True)
+    case = Case(w, dev, z=strong_z(64), seed=21)
+    plan = case.plan()
+    _, _, _, _, _, _, gz = plan.adjoint_ex(case.O, case.P, case.Im, None, case.bg_t)
+    st = AdamState(plan, 1e-3, 1e-3, with_z_gradient=True)
+    plan.step(st, case.O.clone(), case.P.clone(), case.Im, None, case.bg_t)
+    assert torch.equal(st.g_z, gz)                                  # same deterministic pass
+    plan.close()
