@@ -30,6 +30,8 @@ Readings of points where the paper is silent (each also recorded in the design n
 * background N(rho) lives on the model grid and is added before the remap;
 * losses: amplitude  sum (sqrt(I+eps) - sqrt(Ihat))^2, Poisson deviance
   sum (I+eps) - Ihat - Ihat*log((I+eps)/Ihat) with 0*log(.) := 0; no normalisation;
+  mixed Poisson-Gaussian with read-noise variance s2: the Poisson deviance of
+  (I+eps+s2, max(Ihat+s2, 0)) (the shifted-Poisson approximation);
 * gradient convention g = dL/dRe + i dL/dIm (complex parameters);
 * Adam acts on real and imaginary parts as separate real parameters.
 
@@ -254,10 +256,20 @@ def frame_mask(mask: Optional[np.ndarray], j: int, F: int, taps: Optional[RemapT
 # losses (Section "Universal Ptychography Algorithm")
 # ----------------------------------------------------------------------------
 
-def loss_terms(I: np.ndarray, Ihat: np.ndarray, kind: str, eps: float) -> np.ndarray:
-    """Per-pixel loss.  amplitude: (sqrt(I+eps) - sqrt(Ihat))^2; Poisson: deviance."""
-    Ie = I + eps
-    Ihat = Ihat.astype(np.float64)
+def _shifted(I, Ihat, kind, eps):
+    """Mixed Poisson-Gaussian noise (MLE with mixed statistics, Section "Universal
+    Ptychography Algorithm"), kind = ("poisson_gaussian", s2): the shifted-Poisson reading,
+    Ihat + s2 taken as Poisson with mean I + eps + s2 (Ihat + s2 clipped at 0)."""
+    if isinstance(kind, tuple) and kind[0] == "poisson_gaussian":
+        s2 = float(kind[1])
+        return I + eps + s2, np.maximum(Ihat.astype(np.float64) + s2, 0.0), "poisson"
+    return I + eps, Ihat.astype(np.float64), kind
+
+
+def loss_terms(I: np.ndarray, Ihat: np.ndarray, kind, eps: float) -> np.ndarray:
+    """Per-pixel loss.  amplitude: (sqrt(I+eps) - sqrt(Ihat))^2; Poisson: deviance; mixed
+    Poisson-Gaussian: the Poisson deviance of the shifted arguments (see _shifted)."""
+    Ie, Ihat, kind = _shifted(I, Ihat, kind, eps)
     if kind == "amplitude":
         return (np.sqrt(Ie) - np.sqrt(Ihat)) ** 2
     if kind == "poisson":
@@ -267,10 +279,10 @@ def loss_terms(I: np.ndarray, Ihat: np.ndarray, kind: str, eps: float) -> np.nda
     raise ValueError(kind)
 
 
-def loss_derivative(I: np.ndarray, Ihat: np.ndarray, kind: str, eps: float) -> np.ndarray:
-    """dL/dI per pixel.  amplitude: 1 - sqrt(Ihat)/sqrt(I+eps); Poisson: 1 - Ihat/(I+eps)."""
-    Ie = I + eps
-    Ihat = Ihat.astype(np.float64)
+def loss_derivative(I: np.ndarray, Ihat: np.ndarray, kind, eps: float) -> np.ndarray:
+    """dL/dI per pixel.  amplitude: 1 - sqrt(Ihat)/sqrt(I+eps); Poisson: 1 - Ihat/(I+eps);
+    mixed Poisson-Gaussian: 1 - (Ihat+s2)/(I+eps+s2)."""
+    Ie, Ihat, kind = _shifted(I, Ihat, kind, eps)
     if kind == "amplitude":
         return 1.0 - np.sqrt(Ihat) / np.sqrt(Ie)
     if kind == "poisson":

@@ -634,3 +634,55 @@ def test_z_gradient_matches_central_finite_differences(kind):
     fd = (orc.loss(w.O0, w.P0, w.pos, Ih, kind, 1e-3, w.sigma, w.bg, None, tp) -
           orc.loss(w.O0, w.P0, w.pos, Ih, kind, 1e-3, w.sigma, w.bg, None, tm)) / (2 * h)
     assert abs(fd - gz) <= 1e-5 * abs(gz) + 50 * 2.2e-16 * abs(L0) / h, (fd, gz)
+
+
+# ----------------------------------------------------------------------------
+# mixed Poisson-Gaussian loss (shifted-Poisson reading)
+# ----------------------------------------------------------------------------
+
+def test_mixed_loss_reduces_to_poisson_and_vanishes_at_its_minimum():
+    rng = np.random.default_rng(70)
+    I = rng.uniform(0.0, 50.0, size=200)
+    Ih = rng.poisson(I).astype(np.float64)
+    eps = 1e-3
+    assert np.array_equal(orc.loss_terms(I, Ih, ("poisson_gaussian", 0.0), eps), orc.loss_terms(I, Ih, "poisson", eps))
+    s2 = 4.0
+    # each term is >= 0 and vanishes, with its derivative, where I + eps equals Ihat
+    t = orc.loss_terms(I, Ih, ("poisson_gaussian", s2), eps)
+    assert np.all(t >= -1e-12)
+    at = orc.loss_terms(Ih - eps, Ih, ("poisson_gaussian", s2), eps)
+    dt = orc.loss_derivative(Ih - eps, Ih, ("poisson_gaussian", s2), eps)
+    assert np.abs(at).max() < 1e-10 and np.abs(dt).max() < 1e-12
+
+
+def test_mixed_loss_derivative_and_gaussian_limit():
+    rng = np.random.default_rng(71)
+    I = rng.uniform(1.0, 30.0, size=100)
+    Ih = I + rng.normal(0.0, 2.0, size=100)
+    kind = ("poisson_gaussian", 9.0)
+    h = 1e-6
+    fd = (orc.loss_terms(I + h, Ih, kind, 0.0) - orc.loss_terms(I - h, Ih, kind, 0.0)) / (2 * h)
+    assert rel(orc.loss_derivative(I, Ih, kind, 0.0), fd) < 1e-7
+    # read noise much larger than the misfit: the deviance becomes the Gaussian
+    # (I - Ihat)^2 / (2 (Ihat + s2)) with the measured-plus-read-noise variance
+    big = ("poisson_gaussian", 1e6)
+    gauss = (I - Ih) ** 2 / (2 * (Ih + 1e6))
+    assert rel(orc.loss_terms(I, Ih, big, 0.0), gauss) < 1e-4
+
+
+def test_mixed_loss_gradient_matches_finite_differences():
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=72, remap=True, loss="poisson", with_bg=True)
+    taps = orc.remap_taps(w.F, 2e-3, 15e-6, math.radians(70))
+    rng = np.random.default_rng(73)
+    clean = orc.predict(w.O_true, w.P_true, w.pos, None, w.bg, taps)
+    Ih = syn.poisson_measure(clean, 10) + rng.normal(0.0, 1.5, size=clean.shape)
+    kind = ("poisson_gaussian", 2.25)
+    args = (w.pos, Ih, kind, 1e-3, None, w.bg, None, taps)
+    _, gO, gP = orc.gradient(w.O0, w.P0, *args)
+    dO = [crandn(rng, *o.shape) for o in w.O0]
+    dP = crandn(rng, *w.P0.shape)
+    h = 1e-6
+    Lp = orc.loss([o + h * d for o, d in zip(w.O0, dO)], w.P0 + h * dP, *args)
+    Lm = orc.loss([o - h * d for o, d in zip(w.O0, dO)], w.P0 - h * dP, *args)
+    an = sum(np.real(np.vdot(g, d)) for g, d in zip(gO, dO)) + np.real(np.vdot(gP, dP))
+    assert abs((Lp - Lm) / (2 * h) - an) < 1e-6 * abs(an)
