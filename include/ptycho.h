@@ -91,6 +91,9 @@ extern "C" {
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */
+/* Mixed Poisson-Gaussian noise (the paper's MLE with mixed statistics), shifted-Poisson
+ * reading: the Poisson deviance of (I + eps + s2, max(Ihat + s2, 0)), s2 = read_noise_var. */
+#define PTYCHO_LOSS_POISSON_GAUSSIAN 2
 
 typedef struct ptycho_plan ptycho_plan_t;
 
@@ -110,7 +113,7 @@ typedef struct {
   double det_pixel;         /* camera pixel pitch, metres (15 um)                       */
   double tilt_rad;          /* angle of incidence from the surface normal (70 degrees)  */
   int32_t remap;            /* 1: apply the tilted-plane remap inside f5; 0: identity   */
-  int32_t loss;             /* PTYCHO_LOSS_AMPLITUDE or PTYCHO_LOSS_POISSON             */
+  int32_t loss;             /* PTYCHO_LOSS_AMPLITUDE, _POISSON or _POISSON_GAUSSIAN     */
   float eps;                /* intensity floor added to I in the loss and its gradient  */
   int64_t scratch_bytes;    /* FFT scratch budget in bytes; 0 = library default (about 128
                                evaluations per batch, at most 2 GiB)                  */
@@ -119,6 +122,8 @@ typedef struct {
   int32_t flags;            /* PTYCHO_FLAG_* variants; 0 = defaults                      */
   int32_t col_groups;       /* mode groups of the column passes (partial intensity sums
                                per position); 0 = library default                       */
+  float read_noise_var;     /* Gaussian read-noise variance s2 (photons^2, >= 0) of
+                               PTYCHO_LOSS_POISSON_GAUSSIAN; ignored by the other losses */
 } ptycho_geom_t;
 
 /* Adam state (Kingma & Ba), cited by the paper as its optimiser.  Real and imaginary

@@ -23,6 +23,7 @@ class Geom(ctypes.Structure):
         ("remap", ctypes.c_int32), ("loss", ctypes.c_int32), ("eps", ctypes.c_float),
         ("scratch_bytes", ctypes.c_int64), ("overlap", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("col_groups", ctypes.c_int32),
+        ("read_noise_var", ctypes.c_float),
     ]
 
 

@@ -15,7 +15,7 @@ import torch
 
 from . import _native
 
-LOSS_CODES = {"amplitude": 0, "poisson": 1}
+LOSS_CODES = {"amplitude": 0, "poisson": 1, "poisson_gaussian": 2}
 FLAG_RECOMPUTE_COLUMNS = 1
 FLAG_OBJ_GRAD_ATOMIC = 2
 FLAG_KEEP_PSI = 4
@@ -61,7 +61,7 @@ def unpack_objects(flat: torch.Tensor, shapes) -> list:
 def geom_struct(F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = "amplitude", eps: float = 0.0,
                 remap: bool = False, z: float = 88e-3, det_pixel: float = 15e-6,
                 tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0, overlap: int = 0,
-                flags: int = 0, col_groups: int = 0):
+                flags: int = 0, col_groups: int = 0, read_noise_var: float = 0.0):
     """A ``ptycho_geom_t`` and the host arrays it points to (keep both alive while used)."""
     keep = {
         "h": np.ascontiguousarray([int(s_[0]) for s_ in obj_shapes], dtype=np.int32),
@@ -83,6 +83,7 @@ def geom_struct(F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = 
     g.overlap = int(overlap)
     g.flags = int(flags)
     g.col_groups = int(col_groups)
+    g.read_noise_var = float(read_noise_var)
     return g, keep
 
 
@@ -92,7 +93,7 @@ class Plan:
     def __init__(self, F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = "amplitude",
                  eps: float = 0.0, remap: bool = False, z: float = 88e-3, det_pixel: float = 15e-6,
                  tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0, overlap: int = 0,
-                 flags: int = 0, col_groups: int = 0):
+                 flags: int = 0, col_groups: int = 0, read_noise_var: float = 0.0):
         self.F, self.L, self.M, self.J = int(F), int(L), int(M), int(J)
         self.remap = bool(remap)
         self.obj_shapes = [(int(h), int(w)) for (h, w) in obj_shapes]
@@ -100,7 +101,7 @@ class Plan:
         g, self._keep = geom_struct(F, L, M, J, obj_shapes, pos, loss=loss, eps=eps, remap=remap, z=z,
                                     det_pixel=det_pixel, tilt_rad=tilt_rad, lambdas=lambdas,
                                     scratch_bytes=scratch_bytes, overlap=overlap, flags=flags,
-                                    col_groups=col_groups)
+                                    col_groups=col_groups, read_noise_var=read_noise_var)
         self._geom = g
         h = ctypes.c_void_p()
         _check(_native.lib().ptycho_plan_create(ctypes.byref(g), ctypes.byref(h)), "ptycho_plan_create")

@@ -373,7 +373,8 @@ struct LossArgs {
   const uint8_t* mask;           // null, [F][F] or [J][F][F]
   int mask_per_frame;
   float eps;
-  int loss_kind;                 // 0 amplitude, 1 Poisson
+  int loss_kind;                 // 0 amplitude, 1 Poisson, 2 mixed Poisson-Gaussian
+  float read_var;                // s2 of the mixed loss
   float* D;                      // [B][F][F] mask * dL/dI (camera grid), null if not needed
   double* loss_part;             // [nbatch][loss_blocks] or null
   double* sig_part;              // [nbatch][loss_blocks] sums of D * (remapped sum |Psi|^2), or null
@@ -523,8 +524,12 @@ k_loss(KArgs a, LossArgs la) {
       bool use = valid;
       if (la.mask) use = use && (la.mask[(la.mask_per_frame ? (long long)j * FF : 0) + q] != 0);
       if (use) {
-        const float Ih = __ldg(la.Imeas + (long long)j * FF + q);
-        const float Ie = Ic + la.eps;
+        float Ih = __ldg(la.Imeas + (long long)j * FF + q);
+        float Ie = Ic + la.eps;
+        if (la.loss_kind == 2) {                       // shifted Poisson
+          Ie += la.read_var;
+          Ih = fmaxf(Ih + la.read_var, 0.f);
+        }
         if (la.loss_kind == 0) {
           const float se = sqrtf(Ie), diff = se - sqrtf(Ih);
           df_add(th, tl, diff * diff);

@@ -149,6 +149,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.mask_per_frame = c.mask_per_frame;
   la.eps = p.eps;
   la.loss_kind = p.loss_kind;
+  la.read_var = p.read_var;
   la.D = grad ? p.d_D : nullptr;
   la.loss_part = need_loss ? p.d_loss_part : nullptr;
   la.sig_part = grad && c.g_sigma ? p.d_sig_part : nullptr;

@@ -163,6 +163,7 @@ int plain_adjoint(ptycho_plan& p, const CallArgs& c, float2* psi, float* Ibuf, f
   la.mask_per_frame = c.mask_per_frame;
   la.eps = p.eps;
   la.loss_kind = p.loss_kind;
+  la.read_var = p.read_var;
   la.D = Dbuf;                                        // [Bp][F][F], sized by the caller
   la.loss_part = p.d_loss_part;
   la.remap = p.remap;

@@ -15,6 +15,7 @@ struct ptycho_plan {
   int sms = 0;
   int L = 0, M = 0, F = 0, J = 0;
   int remap = 0, loss_kind = 0;
+  float read_var = 0.f;                        // read-noise variance of the mixed loss
   int flags = 0;                               // PTYCHO_FLAG_* variants
   float eps = 0.f;
   int obj_h[ptycho::kMaxL] = {}, obj_w[ptycho::kMaxL] = {};

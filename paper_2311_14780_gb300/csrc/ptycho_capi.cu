@@ -386,7 +386,10 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   *out = nullptr;
   if (g->L < 1 || g->M < 1 || g->J < 1 || !g->obj_h || !g->obj_w || !g->pos) return PTYCHO_EINVAL;
   if (g->L > ptycho::kMaxL || !supported_F(g->F)) return PTYCHO_EUNSUPPORTED;
-  if (g->loss != PTYCHO_LOSS_AMPLITUDE && g->loss != PTYCHO_LOSS_POISSON) return PTYCHO_EINVAL;
+  if (g->loss != PTYCHO_LOSS_AMPLITUDE && g->loss != PTYCHO_LOSS_POISSON && g->loss != PTYCHO_LOSS_POISSON_GAUSSIAN)
+    return PTYCHO_EINVAL;
+  if (g->loss == PTYCHO_LOSS_POISSON_GAUSSIAN && !(g->read_noise_var >= 0.f && isfinite(g->read_noise_var)))
+    return PTYCHO_EINVAL;
   if (!(g->eps >= 0.f) || !isfinite(g->eps)) return PTYCHO_EINVAL;
   if (g->remap && !(g->z > 0.0 && g->det_pixel > 0.0 && isfinite(g->tilt_rad) && fabs(g->tilt_rad) < kPi / 2))
     return PTYCHO_EINVAL;
@@ -409,6 +412,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   p->L = g->L; p->M = g->M; p->F = F; p->J = g->J;
   p->remap = g->remap ? 1 : 0;
   p->loss_kind = g->loss;
+  p->read_var = g->loss == PTYCHO_LOSS_POISSON_GAUSSIAN ? g->read_noise_var : 0.f;
   p->flags = g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_OBJ_GRAD_ATOMIC | PTYCHO_FLAG_NARROW_COLUMNS |
                          PTYCHO_FLAG_NO_PDL);
   // measured: recomputing the column DFT beats keeping Psi from F = 256 up

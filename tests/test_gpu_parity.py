@@ -731,3 +731,35 @@ def test_step_writes_the_z_gradient_of_its_pass(dev):
     plan.step(st, case.O.clone(), case.P.clone(), case.Im, None, case.bg_t)
     assert torch.equal(st.g_z, gz)                                  # same deterministic pass
     plan.close()
+
+
+# ---------------------------------------------------------------------------------------
+# mixed Poisson-Gaussian loss (shifted-Poisson reading)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F,remap", [(64, True), (256, True), (128, False)])
+def test_mixed_poisson_gaussian_loss(dev, F, remap):
+    from paper_2311_14780_gb300 import pack_objects, plan_for
+    w = syn.tiny_workload(F=F, L=2, M=2, n_side=3, step=F // 8, seed=101 + F, remap=remap, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    z = strong_z(F)
+    taps = orc.remap_taps(w.F, z, w.geom.det_pixel, w.geom.tilt_rad) if remap else None
+    s2 = 2.25
+    rng = np.random.default_rng(F)
+    clean = orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps)
+    Ih = (syn.poisson_measure(clean, 30) + rng.normal(0.0, 1.5, size=clean.shape)).astype(np.float32)
+    eps = syn.default_eps(np.maximum(Ih, 0))
+    kind = ("poisson_gaussian", float(np.float32(s2)))
+    plan = plan_for(w, loss="poisson_gaussian", read_noise_var=s2, eps=eps, z=z)
+    O0 = [as_c64_roundtrip(o) for o in w.O0]
+    P0 = as_c64_roundtrip(w.P0)
+    sig = np.asarray(w.sigma, np.float32).astype(np.float64)
+    bg = np.asarray(w.bg, np.float32).astype(np.float64)
+    Ihd = Ih.astype(np.float64)
+    La, gO, gP = plan.adjoint(pack_objects(O0, dev), c64(P0, dev), torch.as_tensor(Ih, device=dev).contiguous(),
+                              f32(sig, dev), f32(bg, dev))
+    Lr, gOr, gPr = orc.gradient(O0, P0, w.pos, Ihd, kind, float(np.float32(eps)), sig, bg, None, taps)
+    gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    assert abs(float(La.item()) - Lr) < TOL_L * abs(Lr)
+    assert rel(gO.cpu().numpy(), gOr) < TOL_G and rel(gP.cpu().numpy(), gPr) < TOL_G
+    plan.close()
