@@ -17,7 +17,9 @@ Readings of points where the paper is silent (each also recorded in the design n
 
 * propagation D_{lambda,z}: orthonormal 2D DFT with the zero frequency moved to
   (F/2, F/2); each wavelength is sampled at its own object pixel size so all
-  wavelengths share one detector grid;
+  wavelengths share one detector grid; optionally the chirp-z (zoom DFT) propagator
+  (1/F) Z psi Z^T with centred indices and zoom zeta_l = lambda_ref / lambda_l, which puts
+  every wavelength on one object grid;
 * integer scan shift: the patch is O_l[y:y+F, x:x+F]; a patch outside the object is
   an error (no wrap-around, no clamping);
 * fractional scan offsets (optional): the integer patch is resampled at r + delta by the
@@ -124,6 +126,35 @@ def f4_propagate(psi: np.ndarray) -> np.ndarray:
 def f4_adjoint(Psi: np.ndarray) -> np.ndarray:
     """Adjoint (= inverse) of f4: undo the centring, orthonormal inverse 2D DFT."""
     return np.fft.ifft2(np.fft.ifftshift(Psi), norm="ortho")
+
+
+def czt_matrix(F: int, zeta: float) -> np.ndarray:
+    """The zoom DFT along one axis: Z[k', n'] = exp(-2 pi i zeta n' k' / F) with both indices
+    centred, n', k' in [-F/2, F/2) (array index = index + F/2).  zeta = 1 is the centred DFT;
+    zeta = lambda_ref / lambda_l samples wavelength l's far field on the detector pixels of a
+    common object grid (the chirp-z propagator the paper uses, Section "Benchmarking ...")."""
+    c = np.arange(F) - F // 2
+    return np.exp(-2j * np.pi * float(zeta) * np.outer(c, c) / F)
+
+
+def f4_propagate_czt(psi: np.ndarray, zeta: float) -> np.ndarray:
+    """f4 with the chirp-z propagator: (1/F) Z psi Z^T (rows, then columns), output centred."""
+    Z = czt_matrix(psi.shape[0], zeta)
+    return Z @ psi @ Z.T / psi.shape[0]
+
+
+def f4_adjoint_czt(Psi: np.ndarray, zeta: float) -> np.ndarray:
+    """Adjoint of f4_propagate_czt: (1/F) Z^H Psi conj(Z)."""
+    Z = czt_matrix(Psi.shape[0], zeta)
+    return Z.conj().T @ Psi @ Z.conj() / Psi.shape[0]
+
+
+def _prop(psi, zeta, l):
+    return f4_propagate(psi) if zeta is None else f4_propagate_czt(psi, zeta[l])
+
+
+def _prop_adj(Psi, zeta, l):
+    return f4_adjoint(Psi) if zeta is None else f4_adjoint_czt(Psi, zeta[l])
 
 
 # ----------------------------------------------------------------------------
@@ -305,8 +336,9 @@ def frame_patch(O_l, pos, l, j, F, delta=None):
     return p if delta is None else f2_subpixel(p, delta[l][j])
 
 
-def frame_fields(O, P, pos, j, sigma=None, delta=None):
-    """Exit waves and propagated fields Psi_{j,l,m} for one frame (f1..f4)."""
+def frame_fields(O, P, pos, j, sigma=None, delta=None, zeta=None):
+    """Exit waves and propagated fields Psi_{j,l,m} for one frame (f1..f4); zeta [L] selects the
+    chirp-z propagator with zoom zeta[l] instead of the DFT."""
     L, M, F = P.shape[0], P.shape[1], P.shape[2]
     s = _sigma(sigma, j)
     patches, Psi = [], np.empty((L, M, F, F), np.complex128)
@@ -314,38 +346,40 @@ def frame_fields(O, P, pos, j, sigma=None, delta=None):
         p = frame_patch(O[l], pos, l, j, F, delta)
         patches.append(p)
         for m in range(M):
-            Psi[l, m] = f4_propagate(f3_interaction(f1_power(P[l, m], s), p))
+            Psi[l, m] = _prop(f3_interaction(f1_power(P[l, m], s), p), zeta, l)
     return patches, Psi
 
 
-def predict_frame(O, P, pos, j, sigma=None, bg=None, taps=None, delta=None) -> np.ndarray:
+def predict_frame(O, P, pos, j, sigma=None, bg=None, taps=None, delta=None, zeta=None) -> np.ndarray:
     """Eq. 1 for frame j: remap( sum_l sum_m |D[sigma_j P_lm O_l(r - s_j)]|^2 + N )."""
-    _, Psi = frame_fields(O, P, pos, j, sigma, delta)
+    _, Psi = frame_fields(O, P, pos, j, sigma, delta, zeta)
     I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
     return f5_measure(I_sum, bg, taps)
 
 
-def predict(O, P, pos, sigma=None, bg=None, taps=None, frames=None, delta=None) -> np.ndarray:
+def predict(O, P, pos, sigma=None, bg=None, taps=None, frames=None, delta=None, zeta=None) -> np.ndarray:
     """Predicted camera-grid patterns for the requested frames (default: all)."""
     J = pos.shape[1]
     frames = range(J) if frames is None else frames
-    return np.stack([predict_frame(O, P, pos, j, sigma, bg, taps, delta) for j in frames])
+    return np.stack([predict_frame(O, P, pos, j, sigma, bg, taps, delta, zeta) for j in frames])
 
 
-def loss(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None, delta=None) -> float:
+def loss(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None, delta=None,
+         zeta=None) -> float:
     """Total loss over the requested frames and their masked pixels."""
     F = P.shape[2]
     J = pos.shape[1]
     frames = range(J) if frames is None else frames
     total = 0.0
     for j in frames:
-        Ic = predict_frame(O, P, pos, j, sigma, bg, taps, delta)
+        Ic = predict_frame(O, P, pos, j, sigma, bg, taps, delta, zeta)
         mk = frame_mask(mask, j, F, taps)
         total += float(loss_terms(Ic, Imeas[j], kind, eps)[mk].sum())
     return total
 
 
-def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None, delta=None):
+def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=None, frames=None, delta=None,
+             zeta=None):
     """Loss and its gradient (dL/dRe + i dL/dIm) with respect to every O_l and P_lm.
 
     For each frame: forward fields Psi_{lm}; I = sum |Psi|^2 (+bg); camera pattern R I;
@@ -362,7 +396,7 @@ def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=N
     total = 0.0
     for j in frames:
         s = _sigma(sigma, j)
-        patches, Psi = frame_fields(O, P, pos, j, sigma, delta)
+        patches, Psi = frame_fields(O, P, pos, j, sigma, delta, zeta)
         I_sum = (np.abs(Psi) ** 2).sum(axis=(0, 1))
         Ic = f5_measure(I_sum, bg, taps)
         mk = frame_mask(mask, j, F, taps)
@@ -374,7 +408,7 @@ def gradient(O, P, pos, Imeas, kind, eps, sigma=None, bg=None, mask=None, taps=N
             y, x = int(pos[l][j][0]), int(pos[l][j][1])
             g_patch = np.zeros((F, F), np.complex128)
             for m in range(M):
-                chi = f4_adjoint(2.0 * G * Psi[l, m])
+                chi = _prop_adj(2.0 * G * Psi[l, m], zeta, l)
                 gP[l, m] += np.conj(s * patches[l]) * chi
                 g_patch += np.conj(s * P[l, m]) * chi
             if delta is not None:

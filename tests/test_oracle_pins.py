@@ -686,3 +686,81 @@ def test_mixed_loss_gradient_matches_finite_differences():
     Lm = orc.loss([o - h * d for o, d in zip(w.O0, dO)], w.P0 - h * dP, *args)
     an = sum(np.real(np.vdot(g, d)) for g, d in zip(gO, dO)) + np.real(np.vdot(gP, dP))
     assert abs((Lp - Lm) / (2 * h) - an) < 1e-6 * abs(an)
+
+
+# ----------------------------------------------------------------------------
+# chirp-z (zoom DFT) propagator
+# ----------------------------------------------------------------------------
+
+def test_czt_at_unit_zoom_is_the_dft_up_to_a_checkerboard_phase():
+    """With zeta = 1 the zoom DFT of the centred window equals numpy's DFT moved to the centre,
+    times (-1)^(k_row + k_col) (the input index is centred too): same intensities."""
+    rng = np.random.default_rng(80)
+    F = 16
+    x = crandn(rng, F, F)
+    c = np.arange(F) - F // 2
+    sign = (-1.0) ** (c[:, None] + c[None, :])
+    assert rel(orc.f4_propagate_czt(x, 1.0), orc.f4_propagate(x) * sign) < 1e-12
+    assert rel(orc.f4_adjoint_czt(orc.f4_propagate_czt(x, 1.0), 1.0), x) < 1e-12
+
+
+def test_czt_of_a_plane_wave_is_the_closed_form_dirichlet_kernel():
+    """A plane wave of a cycles per window (constant along columns) gives, at output (k, kc),
+    (1/F) D(2 pi (a - zeta k)/F) D(-2 pi zeta kc / F) / F with D the geometric series
+    sum_{n=-F/2}^{F/2-1} exp(i theta n); its peak F^2 / F^2 = 1 sits at k = a / zeta."""
+    F = 32
+    n = np.arange(F) - F // 2
+
+    def D(theta):
+        theta = np.asarray(theta, dtype=np.float64)
+        out = np.empty(theta.shape, np.complex128)
+        small = np.abs(np.exp(1j * theta) - 1.0) < 1e-14
+        out[small] = F
+        th = theta[~small]
+        out[~small] = np.exp(-1j * th * F / 2) * (1 - np.exp(1j * th * F)) / (1 - np.exp(1j * th))
+        return out
+
+    for a, zeta in ((6, 0.75), (-9, 1.5), (4, 0.5), (3, 0.9)):
+        x = np.exp(2j * np.pi * a * n / F)[:, None] * np.ones(F)[None, :] / F
+        Psi = orc.f4_propagate_czt(x, zeta)
+        want = D(2 * np.pi * (a - zeta * n) / F)[:, None] * D(-2 * np.pi * zeta * n / F)[None, :] / F / F
+        assert rel(Psi, want) < 1e-11
+        if float(a / zeta).is_integer():
+            assert abs(abs(Psi[int(a / zeta) + F // 2, F // 2]) - 1.0) < 1e-12
+
+
+def test_czt_adjoint_identity_and_zoom_two_subsamples_the_dft():
+    rng = np.random.default_rng(81)
+    F = 16
+    x, y = crandn(rng, F, F), crandn(rng, F, F)
+    for zeta in (0.83, 1.17):
+        lhs = np.vdot(y, orc.f4_propagate_czt(x, zeta))
+        rhs = np.vdot(orc.f4_adjoint_czt(y, zeta), x)
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # zeta = 2: output k' is the centred DFT at frequency 2 k' (mod F)
+    Zd = orc.czt_matrix(F, 1.0)
+    Z2 = orc.czt_matrix(F, 2.0)
+    c = np.arange(F) - F // 2
+    assert rel(Z2, Zd[(2 * c + F // 2) % F]) < 1e-12
+
+
+@pytest.mark.parametrize("kind", orc.LOSS_KINDS)
+def test_czt_model_gradient_matches_finite_differences(kind):
+    w = syn.tiny_workload(F=16, L=2, M=2, seed=82, remap=True, loss=kind, with_sigma=True, with_bg=True)
+    taps = orc.remap_taps(w.F, 2e-3, 15e-6, math.radians(70))
+    zeta = [1.0, 1.0 / 1.1]
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps, zeta=zeta), 11)
+    args = (w.pos, Ih, kind, 1e-3, w.sigma, w.bg, None, taps)
+    _, gO, gP = orc.gradient(w.O0, w.P0, *args, zeta=zeta)
+    rng = np.random.default_rng(83)
+    dO = [crandn(rng, *o.shape) for o in w.O0]
+    dP = crandn(rng, *w.P0.shape)
+    h = 1e-6
+    Lp = orc.loss([o + h * d for o, d in zip(w.O0, dO)], w.P0 + h * dP, *args, zeta=zeta)
+    Lm = orc.loss([o - h * d for o, d in zip(w.O0, dO)], w.P0 - h * dP, *args, zeta=zeta)
+    an = sum(np.real(np.vdot(g, d)) for g, d in zip(gO, dO)) + np.real(np.vdot(gP, dP))
+    assert abs((Lp - Lm) / (2 * h) - an) < 1e-6 * abs(an)
+    Lt, gOt, gPt = orc.gradient(w.O_true, w.P_true, w.pos, orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, taps,
+                                                                       zeta=zeta), kind, 0.0, w.sigma, w.bg, None,
+                                taps, zeta=zeta)
+    assert abs(Lt) < 1e-18 * float(Ih.sum()) and np.abs(gPt).max() < 1e-10
