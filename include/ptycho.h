@@ -124,6 +124,15 @@ typedef struct {
                                per position); 0 = library default                       */
   float read_noise_var;     /* Gaussian read-noise variance s2 (photons^2, >= 0) of
                                PTYCHO_LOSS_POISSON_GAUSSIAN; ignored by the other losses */
+  const double* zoom;       /* [L] or NULL.  Non-NULL selects the chirp-z propagator (the
+                               paper's, Section "Benchmarking ..."): per wavelength the zoom
+                               DFT Z[k'][n'] = exp(-2 pi i zoom[l] n' k' / F), centred
+                               indices, Psi = (1/F) Z psi Z^T; zoom[l] = lambda_ref /
+                               lambda_l puts every wavelength on one object grid (then
+                               obj shapes and positions can be equal for all l).  Needs
+                               F <= 256 and all modes of a position in the scratch
+                               (PTYCHO_EUNSUPPORTED otherwise); 0 < zoom[l] <= 4.  NULL:
+                               the orthonormal DFT with the DC at F/2.                  */
 } ptycho_geom_t;
 
 /* Adam state (Kingma & Ba), cited by the paper as its optimiser.  Real and imaginary

@@ -24,6 +24,7 @@ class Geom(ctypes.Structure):
         ("scratch_bytes", ctypes.c_int64), ("overlap", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("col_groups", ctypes.c_int32),
         ("read_noise_var", ctypes.c_float),
+        ("zoom", ctypes.POINTER(ctypes.c_double)),
     ]
 
 

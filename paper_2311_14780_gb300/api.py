@@ -61,13 +61,14 @@ def unpack_objects(flat: torch.Tensor, shapes) -> list:
 def geom_struct(F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = "amplitude", eps: float = 0.0,
                 remap: bool = False, z: float = 88e-3, det_pixel: float = 15e-6,
                 tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0, overlap: int = 0,
-                flags: int = 0, col_groups: int = 0, read_noise_var: float = 0.0):
+                flags: int = 0, col_groups: int = 0, read_noise_var: float = 0.0, zoom=None):
     """A ``ptycho_geom_t`` and the host arrays it points to (keep both alive while used)."""
     keep = {
         "h": np.ascontiguousarray([int(s_[0]) for s_ in obj_shapes], dtype=np.int32),
         "w": np.ascontiguousarray([int(s_[1]) for s_ in obj_shapes], dtype=np.int32),
         "pos": np.ascontiguousarray(np.asarray(pos, dtype=np.int32).reshape(L, J, 2)),
         "lam": None if lambdas is None else np.ascontiguousarray(lambdas, dtype=np.float64),
+        "zoom": None if zoom is None else np.ascontiguousarray(zoom, dtype=np.float64).reshape(L),
     }
     g = _native.Geom()
     g.L, g.M, g.F, g.J = int(L), int(M), int(F), int(J)
@@ -84,6 +85,7 @@ def geom_struct(F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = 
     g.flags = int(flags)
     g.col_groups = int(col_groups)
     g.read_noise_var = float(read_noise_var)
+    g.zoom = None if keep["zoom"] is None else keep["zoom"].ctypes.data_as(_native.c_double_p)
     return g, keep
 
 
@@ -93,7 +95,7 @@ class Plan:
     def __init__(self, F: int, L: int, M: int, J: int, obj_shapes, pos, *, loss: str = "amplitude",
                  eps: float = 0.0, remap: bool = False, z: float = 88e-3, det_pixel: float = 15e-6,
                  tilt_rad: float = 1.2217304763960306, lambdas=None, scratch_bytes: int = 0, overlap: int = 0,
-                 flags: int = 0, col_groups: int = 0, read_noise_var: float = 0.0):
+                 flags: int = 0, col_groups: int = 0, read_noise_var: float = 0.0, zoom=None):
         self.F, self.L, self.M, self.J = int(F), int(L), int(M), int(J)
         self.remap = bool(remap)
         self.obj_shapes = [(int(h), int(w)) for (h, w) in obj_shapes]
@@ -101,7 +103,7 @@ class Plan:
         g, self._keep = geom_struct(F, L, M, J, obj_shapes, pos, loss=loss, eps=eps, remap=remap, z=z,
                                     det_pixel=det_pixel, tilt_rad=tilt_rad, lambdas=lambdas,
                                     scratch_bytes=scratch_bytes, overlap=overlap, flags=flags,
-                                    col_groups=col_groups, read_noise_var=read_noise_var)
+                                    col_groups=col_groups, read_noise_var=read_noise_var, zoom=zoom)
         self._geom = g
         h = ctypes.c_void_p()
         _check(_native.lib().ptycho_plan_create(ctypes.byref(g), ctypes.byref(h)), "ptycho_plan_create")

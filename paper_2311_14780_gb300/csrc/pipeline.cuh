@@ -93,6 +93,12 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_cols<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_cols<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
+  if constexpr (F <= 256) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztRowCfg<F>::smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_col_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztColCfg<F>::smem_fwd);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_col_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztColCfg<F>::smem_adj);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztRowAdjCfg<F>::smem);
+  }
   if (e == cudaSuccess) e = set_cols_smem<F, 0>();
   if (e == cudaSuccess) e = set_cols_smem<F, 4>();
   if (e != cudaSuccess) return PTYCHO_ECUDA;
@@ -159,6 +165,8 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.tap_dz = p.d_tap_dz;
   la.z_part = grad && c.g_z ? p.d_z_part : nullptr;
 
+  CztArgs ct{p.d_czt_chirp, p.d_czt_hf, p.d_czt_ha, p.d_czt_tw2};
+  if (p.czt && (F > 256 || p.nchunks != 1 || p.d_delta)) return PTYCHO_EUNSUPPORTED;
   AdjArgs aa{};
   aa.D = p.d_D;
   aa.rt_ptr = p.d_rt_ptr;
@@ -240,6 +248,16 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
     for (int ch = 0; ch < p.nchunks; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
+      if constexpr (F <= 256) {
+        if (p.czt) {                                  // chirp-z propagator
+          PTY_LAUNCH(p, kRowFwd, cs, launch_pdl(k_czt_row_fwd<F>, dim3(F / CztRowCfg<F>::RPB, p.L, a.nb),
+                                                CztRowCfg<F>::threads, CztRowCfg<F>::smem, cs, c.O, c.P, S, a, ct));
+          PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_czt_col_fwd<F>, dim3(F / CztColCfg<F>::W, p.G, a.nb),
+                                                CztColCfg<F>::threads, CztColCfg<F>::smem_fwd, cs, (const float2*)S, Ip,
+                                                a, ct));
+          continue;
+        }
+      }
       if (fwd_l)
         PTY_LAUNCH(p, kRowFwd, cs,
                    launch_pdl(k_row_fwd_l<F>, dim3(F / p.rpb_adj, p.L, p.nsplit_fwd), FftShape<F>::N1 * p.M * p.rpb_adj,
@@ -274,6 +292,23 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       const dim3 col_grid(F / ColCfg<F>::W, p.G, a.nb);
+      if constexpr (F <= 256) {
+        if (p.czt) {                                  // chirp-z propagator
+          PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_czt_col_adj<F>, dim3(F / CztColCfg<F>::W, p.G, a.nb),
+                                                CztColCfg<F>::threads, CztColCfg<F>::smem_adj, cs, S, a, aa, ct));
+          if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_radj[(k - 1) % nsets], 0) != cudaSuccess)
+            return PTYCHO_ECUDA;
+          PTY_LAUNCH(p, kRowAdj, cs, launch_pdl(k_czt_row_adj<F>, dim3(F / CztRowAdjCfg<F>::RPB, a.chunk_len),
+                                                CztRowAdjCfg<F>::threads, CztRowAdjCfg<F>::smem, cs, c.O, c.P, S, c.gP,
+                                                a, ct));
+          if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+          if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_og[(k - 1) % nsets], 0) != cudaSuccess)
+            return PTYCHO_ECUDA;
+          PTY_LAUNCH(p, kObjGrad, cs, launch_pdl(k_obj_grad<F>, dim3(max_tiles, p.L), 256, 0, cs, S, c.gO, a));
+          if (nsets > 1 && cudaEventRecord(p.ev_og[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+          continue;
+        }
+      }
       if (!store && rerun_rows)
         PTY_LAUNCH(p, kRowFwd, cs,
                    launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));

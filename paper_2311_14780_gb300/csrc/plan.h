@@ -9,6 +9,7 @@
 #include "../../include/ptycho.h"
 #include "kernels.cuh"
 #include "shift.cuh"
+#include "czt.cuh"
 
 struct ptycho_plan {
   int dev = 0;
@@ -16,6 +17,12 @@ struct ptycho_plan {
   int L = 0, M = 0, F = 0, J = 0;
   int remap = 0, loss_kind = 0;
   float read_var = 0.f;                        // read-noise variance of the mixed loss
+  // chirp-z propagator (geometry zoom != NULL): Bluestein tables on the device
+  int czt = 0;
+  float2* d_czt_chirp = nullptr;               // [L][F]
+  float2* d_czt_hf = nullptr;                  // [L][2F]
+  float2* d_czt_ha = nullptr;                  // [L][2F]
+  float2* d_czt_tw2 = nullptr;                 // [2F]
   int flags = 0;                               // PTYCHO_FLAG_* variants
   float eps = 0.f;
   int obj_h[ptycho::kMaxL] = {}, obj_w[ptycho::kMaxL] = {};

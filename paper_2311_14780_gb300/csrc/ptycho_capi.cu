@@ -216,6 +216,63 @@ int load_remap(ptycho_plan* p) {
   return rc;
 }
 
+// Bluestein tables of the chirp-z propagator, in FP64, rounded to float2:
+//   chirp[l][n] = exp(-i pi zeta (n - F/2)^2 / F);
+//   hf[l] = DFT_2F of the kernel h(m) = exp(+i pi zeta m^2 / F) for |m| < F at index m mod 2F
+//           (index F: 0), ha[l] = DFT_2F of conj(h);  tw2[k2*N1 + t] = exp(-2 pi i t k2 / 2F).
+int load_czt(ptycho_plan* p, const double* zoom) {
+  const int F = p->F, N = 2 * F, L = p->L;
+  int N1 = 0;
+  switch (F) {
+    case 64: N1 = ptycho::FftShape<64>::N1; break;
+    case 128: N1 = ptycho::FftShape<128>::N1; break;
+    default: N1 = ptycho::FftShape<256>::N1; break;
+  }
+  std::vector<float2> chirp((size_t)L * F), hf((size_t)L * N), ha((size_t)L * N), tw2((size_t)N);
+  std::vector<double> hr(N), hi(N);
+  for (int l = 0; l < L; ++l) {
+    const double z = zoom[l];
+    for (int n = 0; n < F; ++n) {
+      const double c = (double)(n - F / 2), ang = -kPi * z * c * c / F;
+      chirp[(size_t)l * F + n] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    for (int m = 0; m < N; ++m) {
+      const int mm = m < F ? m : m - N;
+      if (m == F) { hr[m] = hi[m] = 0.0; continue; }
+      const double ang = kPi * z * (double)mm * (double)mm / F;
+      hr[m] = cos(ang);
+      hi[m] = sin(ang);
+    }
+    for (int k = 0; k < N; ++k) {
+      double fr = 0.0, fi = 0.0, ar = 0.0, ai = 0.0;
+      for (int m = 0; m < N; ++m) {
+        const double ang = -2.0 * kPi * (double)(((long long)k * m) % N) / N;
+        const double c = cos(ang), sn = sin(ang);
+        fr += hr[m] * c - hi[m] * sn;                 // h * e
+        fi += hr[m] * sn + hi[m] * c;
+        ar += hr[m] * c + hi[m] * sn;                 // conj(h) * e
+        ai += hr[m] * sn - hi[m] * c;
+      }
+      hf[(size_t)l * N + k] = make_float2((float)fr, (float)fi);
+      ha[(size_t)l * N + k] = make_float2((float)ar, (float)ai);
+    }
+  }
+  for (int t = 0; t < N1; ++t)
+    for (int k2 = 0; k2 < N / N1; ++k2) {
+      const double ang = -2.0 * kPi * (double)((t * k2) % N) / N;
+      tw2[(size_t)k2 * N1 + t] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+  int rc = dalloc(p, &p->d_czt_chirp, (long long)L * F);
+  rc = rc ? rc : dalloc(p, &p->d_czt_hf, (long long)L * N);
+  rc = rc ? rc : dalloc(p, &p->d_czt_ha, (long long)L * N);
+  rc = rc ? rc : dalloc(p, &p->d_czt_tw2, (long long)N);
+  rc = rc ? rc : upload(p->d_czt_chirp, chirp.data(), (long long)L * F);
+  rc = rc ? rc : upload(p->d_czt_hf, hf.data(), (long long)L * N);
+  rc = rc ? rc : upload(p->d_czt_ha, ha.data(), (long long)L * N);
+  rc = rc ? rc : upload(p->d_czt_tw2, tw2.data(), (long long)N);
+  return rc;
+}
+
 void free_plan(ptycho_plan* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -230,7 +287,8 @@ void free_plan(ptycho_plan* p) {
   void* ptrs[] = {p->d_pos, p->d_ident, p->d_tw, p->d_tap_base, p->d_tap_w, p->d_rt_ptr, p->d_rt_idx,
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
                   p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs, p->d_shT, p->d_shQ, p->d_shP,
-                  p->d_dpart, p->d_gdelta, p->d_tap_dz, p->d_z_part};
+                  p->d_dpart, p->d_gdelta, p->d_tap_dz, p->d_z_part, p->d_czt_chirp, p->d_czt_hf,
+                  p->d_czt_ha, p->d_czt_tw2};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -390,6 +448,11 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     return PTYCHO_EINVAL;
   if (g->loss == PTYCHO_LOSS_POISSON_GAUSSIAN && !(g->read_noise_var >= 0.f && isfinite(g->read_noise_var)))
     return PTYCHO_EINVAL;
+  if (g->zoom) {
+    for (int l = 0; l < g->L; ++l)
+      if (!(g->zoom[l] > 0.0 && g->zoom[l] <= 4.0)) return PTYCHO_EINVAL;
+    if (g->F > 256) return PTYCHO_EUNSUPPORTED;       // the 2F-point transform needs F/N1 = 16
+  }
   if (!(g->eps >= 0.f) || !isfinite(g->eps)) return PTYCHO_EINVAL;
   if (g->remap && !(g->z > 0.0 && g->det_pixel > 0.0 && isfinite(g->tilt_rad) && fabs(g->tilt_rad) < kPi / 2))
     return PTYCHO_EINVAL;
@@ -514,6 +577,20 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     }
   }
 
+  // chirp-z propagator: its own passes (the per-mode row adjoint, the mode-group columns with
+  // the column transform recomputed in the adjoint); all modes of a position in the scratch
+  if (g->zoom) {
+    if (!p->store) {
+      free_plan(p);
+      return PTYCHO_EUNSUPPORTED;
+    }
+    p->czt = 1;
+    p->adj_l = 0;
+    p->fwd_l = 0;
+    p->col_staged = 0;
+    p->flags |= PTYCHO_FLAG_RECOMPUTE_COLUMNS;
+  }
+
   int rc = PTYCHO_OK;
   const long long FF = (long long)F * F;
   rc = rc ? rc : dalloc(p, &p->d_pos, (long long)g->L * g->J * 2);
@@ -559,7 +636,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     }
     const long long rows = (long long)p->B * p->C * F;
     // measured: the staged column passes pay off from F = 512 up
-    p->has_tma = (g->flags & PTYCHO_FLAG_NO_TMA) ? 0 : ((g->flags & PTYCHO_FLAG_TMA) || F >= 512) ? 1 : 0;
+    p->has_tma = (g->flags & PTYCHO_FLAG_NO_TMA) || p->czt ? 0 : ((g->flags & PTYCHO_FLAG_TMA) || F >= 512) ? 1 : 0;
     for (int i = 0; i < p->nsets; ++i)
       if (p->has_tma && !make_column_map(&p->tmap_S[i], p->d_S + (long long)i * p->B * p->C * FF, F, rows, W))
         p->has_tma = 0;
@@ -596,6 +673,7 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     rc = rc ? rc : dalloc(p, &p->d_z_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
     rc = rc ? rc : load_remap(p);
   }
+  if (!rc && p->czt) rc = load_czt(p, g->zoom);
   if (rc) { free_plan(p); return rc; }
   *out = p;
   return PTYCHO_OK;
@@ -694,7 +772,7 @@ int ptycho_plan_set_offsets(ptycho_plan_t* p, float* delta) {
     p->d_delta = nullptr;
     return PTYCHO_OK;
   }
-  if (!p->store || !p->adj_l_ok) return PTYCHO_EUNSUPPORTED;
+  if (!p->store || !p->adj_l_ok || p->czt) return PTYCHO_EUNSUPPORTED;
   if (!p->d_shT) {
     const long long n = (long long)p->nsets * p->B * p->L * p->F * p->F;
     int W = 0;

@@ -763,3 +763,50 @@ def test_mixed_poisson_gaussian_loss(dev, F, remap):
     assert abs(float(La.item()) - Lr) < TOL_L * abs(Lr)
     assert rel(gO.cpu().numpy(), gOr) < TOL_G and rel(gP.cpu().numpy(), gPr) < TOL_G
     plan.close()
+
+
+# ---------------------------------------------------------------------------------------
+# chirp-z (zoom DFT) propagator
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F,loss,remap", [(64, "poisson", True), (128, "amplitude", False), (256, "poisson", True)])
+def test_czt_propagator_against_the_oracle(dev, F, loss, remap):
+    from paper_2311_14780_gb300 import pack_objects, plan_for
+    w = syn.tiny_workload(F=F, L=3, M=2, n_side=3, step=F // 8, seed=111 + F, remap=remap, loss=loss,
+                          with_sigma=True, with_bg=True)
+    zeta = [1.0, 1.0 / 1.1, 1.0 / 1.2]                        # lambda_1 / lambda_l
+    case = Case(w, dev, z=strong_z(F), mask_kind="shared", seed=22)
+    clean = orc.predict(w.O_true, w.P_true, w.pos, w.sigma, w.bg, case.taps, zeta=zeta)
+    Ih = syn.poisson_measure(clean, 40 + F)
+    eps = syn.default_eps(Ih)
+    plan = plan_for(w, loss=loss, eps=eps, z=case.z, zoom=zeta, scratch_bytes=2 * 6 * F * F * 8)
+    Im = torch.as_tensor(Ih, device=dev).contiguous()
+    Ip = plan.forward(case.O, case.P, case.sig_t, case.bg_t).cpu().numpy()
+    Ir = orc.predict(case.O0, case.P0, w.pos, case.sigma, case.bg, case.taps, zeta=zeta)
+    assert rel(Ip, Ir) < TOL_I
+    La, gO, gP, gs, gb, _, _ = plan.adjoint_ex(case.O, case.P, Im, case.sig_t, case.bg_t, case.mask_t)
+    Lr, gOr, gPr = orc.gradient(case.O0, case.P0, w.pos, Ih, loss, eps, case.sigma, case.bg, case.mask, case.taps,
+                                zeta=zeta)
+    gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    assert abs(float(La.item()) - Lr) < TOL_L * abs(Lr)
+    assert rel(gO.cpu().numpy(), gOr) < TOL_G and rel(gP.cpu().numpy(), gPr) < TOL_G
+    assert plan.status() == 0
+    plan.close()
+
+
+def test_czt_at_unit_zoom_gives_the_dft_intensities_and_rejects_what_it_cannot_do(dev):
+    from paper_2311_14780_gb300 import PtychoError, plan_for
+    w = syn.tiny_workload(F=128, L=2, M=2, n_side=3, step=14, seed=113, remap=True, loss="poisson", with_bg=True)
+    case = Case(w, dev, z=strong_z(128), seed=23)
+    p_dft = case.plan()
+    p_czt = case.plan(zoom=[1.0, 1.0])
+    I1 = p_dft.forward(case.O, case.P, None, case.bg_t).cpu().numpy()
+    I2 = p_czt.forward(case.O, case.P, None, case.bg_t).cpu().numpy()
+    assert rel(I2, I1) < TOL_I
+    with pytest.raises(PtychoError):
+        p_czt.set_offsets(torch.zeros(w.L, w.J, 2, dtype=torch.float32, device=dev))
+    p_dft.close()
+    p_czt.close()
+    w5 = syn.tiny_workload(F=512, L=1, M=1, n_side=2, step=64, seed=114)
+    with pytest.raises(PtychoError):
+        plan_for(w5, zoom=[1.0])
