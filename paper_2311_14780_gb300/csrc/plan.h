@@ -137,6 +137,13 @@ enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLoss
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);
 void prof_end(ptycho_plan& p, long long idx, cudaStream_t st);
 
+// ptycho_plan_create with a target of evaluations per position batch (the public entry
+// point's default favours throughput; the serving engine keeps sites' batches small, because
+// its concurrency comes from the many sites in a tick and each site's scratch counts against
+// the HBM budget).
+int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** out);
+constexpr long long kServeBatchEvals = 128;
+
 // Defined once per frame size in kern_<F>.cu.
 template <int F> int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st);
 template <int F> int prepare_kernels();

@@ -154,7 +154,8 @@ using ptycho::CallKind;
 namespace {
 
 constexpr long long kMaxScratch = 2ll << 30;   // default upper bound of the FFT scratch
-constexpr long long kBatchEvals = 128;         // evaluations per batch the default aims for
+constexpr long long kBatchEvals = 1200;        // evaluations per batch the default aims for
+constexpr long long kMinBatches = 3;           // and at least this many batches per call (overlap)
 constexpr long long kBatchRows = 32768;        // and at least this many 1D FFT rows per pass
 constexpr int kDefaultOverlap = 3;             // position batches in flight
 constexpr double kPi = 3.14159265358979323846;
@@ -440,6 +441,14 @@ const char* ptycho_strerror(int code) {
 }
 
 int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
+  return ptycho::create_plan(g, kBatchEvals, out);
+}
+
+}  // extern "C"
+
+namespace ptycho {
+
+int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** out) {
   if (!g || !out) return PTYCHO_EINVAL;
   *out = nullptr;
   if (g->L < 1 || g->M < 1 || g->J < 1 || !g->obj_h || !g->obj_w || !g->pos) return PTYCHO_EINVAL;
@@ -508,8 +517,10 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
     p->C = (int)LM;
     p->nchunks = 1;
     long long B = p->scratch_budget / (LM * FF8);
-    if (g->scratch_bytes <= 0)
-      B = std::min<long long>(B, std::max((kBatchEvals + LM - 1) / LM, (kBatchRows + LM * F - 1) / (LM * F)));
+    if (g->scratch_bytes <= 0) {
+      B = std::min<long long>(B, std::max((batch_evals + LM - 1) / LM, (kBatchRows + LM * F - 1) / (LM * F)));
+      B = std::min<long long>(B, std::max<long long>(1, (g->J + kMinBatches - 1) / kMinBatches));
+    }
     p->B = (int)std::max<long long>(1, std::min<long long>(B, ptycho::kMaxB));
     p->B = std::min(p->B, g->J);
   } else {
@@ -678,6 +689,10 @@ int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
   *out = p;
   return PTYCHO_OK;
 }
+
+}  // namespace ptycho
+
+extern "C" {
 
 int ptycho_plan_destroy(ptycho_plan_t* p) {
   if (!p) return PTYCHO_OK;

@@ -152,7 +152,7 @@ int ptycho_server_admit(ptycho_server_t* sv, const ptycho_geom_t* geom, const pt
   Site* s = new (std::nothrow) Site();
   if (!s) return PTYCHO_ENOMEM;
   s->data = *site;
-  int rc = ptycho_plan_create(geom, &s->plan);
+  int rc = ptycho::create_plan(geom, ptycho::kServeBatchEvals, &s->plan);
   if (rc) { delete s; return rc; }
   ptycho_plan* p = s->plan;
   const long long FF = (long long)p->F * p->F;
