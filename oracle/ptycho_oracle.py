@@ -29,6 +29,10 @@ Readings of points where the paper is silent (each also recorded in the design n
   sample-plane spatial frequency) to the camera grid, derived from the camera being
   perpendicular to the specular beam (Section "Experimental setup"); taps outside the
   model grid remove the camera pixel from the mask;
+* the same geometry applied once to the data (the paper's preprocessing form): each camera
+  pattern is interpolated at the camera position of every model-grid pixel (the inverse
+  map, with the reflected ray leaving the sample surface) and a mask keeps the pixels whose
+  four taps lie inside the camera crop and inside the value thresholds;
 * background N(rho) lives on the model grid and is added before the remap;
 * losses: amplitude  sum (sqrt(I+eps) - sqrt(Ihat))^2, Poisson deviance
   sum (I+eps) - Ihat - Ihat*log((I+eps)/Ihat) with 0*log(.) := 0; no normalisation;
@@ -48,7 +52,10 @@ fractional offsets: whole-pixel offsets as cyclic rolls, band-limited plane wave
 at the shifted points, unitarity, composition, the adjoint identity, reduction to the
 integer model, and finite differences of the loss in the offsets, O and P; for z: finite
 differences of the fractional model indices and of the loss with the remap rebuilt at z +- h,
-exactness for an intensity linear on the model grid, and zero rate at the specular pixel).  The tilted-plane remap formula itself is a reading of the
+exactness for an intensity linear on the model grid, and zero rate at the specular pixel; for
+the data-side tilt correction: the inverse map undoes the forward map at every camera pixel,
+exactness for patterns affine on the camera, near-identity without tilt, the mask of a
+saturated pixel, and undoing the in-model remap of smooth patterns).  The tilted-plane remap formula itself is a reading of the
 cited geometry and is only partially pinned (identity limit, constants, adjointness,
 the paper's NA and pixel-ratio figures).
 """
@@ -258,6 +265,75 @@ def remap_adjoint(D_cam: np.ndarray, taps: RemapTaps) -> np.ndarray:
     for (ii, jj, w) in _tap_weights(taps):
         np.add.at(out, (ii, jj), w * D_cam)
     return out
+
+
+# ----------------------------------------------------------------------------
+# data-side tilt correction (the remap applied once to the measurements)
+# ----------------------------------------------------------------------------
+
+def tilt_camera_index(F: int, z: float, det_pixel: float, tilt_rad: float, yhat, xhat):
+    """Where the model-grid point (yhat, xhat) (fractional indices of the grid of
+    remap_taps) lies on the camera: the inverse of the map in remap_taps.
+
+    The model index fixes the reflected ray's in-plane direction cosines
+    b = (yhat - F/2) db and a = (xhat - F/2) da.  Rotated by alpha about the camera's x
+    axis, the ray is (a, b + sin(alpha), w) with w = sqrt(1 - a^2 - (b + sin(alpha))^2),
+    taken >= 0 (the reflected ray leaves the sample surface).  In the camera frame its
+    components are d_y = (b + sin) cos - w sin and d_z = (b + sin) sin + w cos, and it
+    meets the camera plane at X = z a / d_z, Y = z d_y / d_z.  Returns (y, x, ok): the
+    fractional camera indices Y/p + F/2 and X/p + F/2, and whether the ray exists and
+    reaches the camera (1 - a^2 - (b + sin)^2 > 0 and d_z > 0)."""
+    c, s = math.cos(tilt_rad), math.sin(tilt_rad)
+    da = det_pixel / z
+    db = da * c
+    b = (np.asarray(yhat, np.float64) - F / 2) * db
+    a = (np.asarray(xhat, np.float64) - F / 2) * da
+    u = b + s
+    w2 = 1.0 - a * a - u * u
+    w = np.sqrt(np.where(w2 > 0, w2, 0.0))
+    dy = u * c - w * s
+    dz = u * s + w * c
+    ok = (w2 > 0) & (dz > 0)
+    dzs = np.where(ok, dz, 1.0)
+    X = z * a / dzs
+    Y = z * dy / dzs
+    return Y / det_pixel + F / 2, X / det_pixel + F / 2, ok
+
+
+def tilt_correct(I_cam: np.ndarray, z: float, det_pixel: float, tilt_rad: float,
+                 lo: float = -math.inf, hi: float = math.inf):
+    """The tilt correction of Section "Experimental setup and ptychography reconstruction",
+    applied once to the data: every camera pattern I_cam[j] (F x F, zero frequency at
+    (F/2, F/2)) is interpolated (bilinear) at the camera position of each model-grid pixel
+    (tilt_camera_index), which puts it on the grid uniform in sample-plane spatial
+    frequency.  It also makes the mask the paper describes: a model pixel is kept when its
+    ray reaches the camera, its four camera taps lie inside the F x F crop
+    (0 <= y < F-1, 0 <= x < F-1), and every tap's value lies in [lo, hi) (the paper's
+    thresholds against noise-corrupted and saturated pixels).  Returns (I_model, mask), both
+    [J][F][F]; I_model is 0 where the mask is 0."""
+    I_cam = np.asarray(I_cam)
+    J, F, _ = I_cam.shape
+    ii, kk = np.mgrid[0:F, 0:F].astype(np.float64)
+    y, x, ok = tilt_camera_index(F, z, det_pixel, tilt_rad, ii, kk)
+    inside = ok & (y >= 0.0) & (y < F - 1) & (x >= 0.0) & (x < F - 1)
+    y0 = np.where(inside, np.floor(np.where(inside, y, 0.0)), 0).astype(np.int64)
+    x0 = np.where(inside, np.floor(np.where(inside, x, 0.0)), 0).astype(np.int64)
+    u = np.where(inside, y - y0, 0.0)
+    v = np.where(inside, x - x0, 0.0)
+    out = np.zeros((J, F, F))
+    mask = np.zeros((J, F, F), bool)
+    for j in range(J):
+        cam = I_cam[j].astype(np.float64)
+        taps = [(cam[y0, x0], (1 - u) * (1 - v)), (cam[y0, x0 + 1], (1 - u) * v),
+                (cam[y0 + 1, x0], u * (1 - v)), (cam[y0 + 1, x0 + 1], u * v)]
+        keep = inside.copy()
+        val = np.zeros((F, F))
+        for t, wt in taps:
+            keep &= (t >= lo) & (t < hi)
+            val += wt * t
+        out[j] = np.where(keep, val, 0.0)
+        mask[j] = keep
+    return out, mask
 
 
 # ----------------------------------------------------------------------------

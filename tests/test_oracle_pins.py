@@ -438,6 +438,100 @@ def test_remap_geometry_against_the_paper_numbers():
 
 
 # ----------------------------------------------------------------------------
+# data-side tilt correction
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("F,z,alpha_deg", [(64, 0.02, 70.0), (256, 0.088, 70.0), (2048, 0.088, 70.0),
+                                           (128, 0.05, 35.0)])
+def test_tilt_inverse_map_undoes_the_remap_geometry(F, z, alpha_deg):
+    """Camera pixel -> fractional model index (remap_taps) -> camera position
+    (tilt_camera_index) returns the pixel: the two maps are each other's inverse."""
+    p, alpha = 15e-6, math.radians(alpha_deg)
+    taps = orc.remap_taps(F, z, p, alpha)
+    y, x, ok = orc.tilt_camera_index(F, z, p, alpha, taps.yhat, taps.xhat)
+    yy, xx = np.mgrid[0:F, 0:F]
+    assert ok.all()
+    assert np.abs(y - yy).max() < 1e-9 * F and np.abs(x - xx).max() < 1e-9 * F
+    # the specular direction sits at the centre of both grids
+    yc, xc, okc = orc.tilt_camera_index(F, z, p, alpha, F / 2, F / 2)
+    assert okc and abs(yc - F / 2) < 1e-9 and abs(xc - F / 2) < 1e-9
+
+
+def test_tilt_correction_reproduces_affine_camera_patterns_exactly():
+    """Bilinear interpolation is exact for patterns affine in the camera indices, so the
+    corrected pattern is the affine function at the mapped camera positions; a swapped
+    axis, weight or tap would break it (different slopes along y and x)."""
+    F, z, p, alpha = 64, 0.02, 15e-6, math.radians(70)
+    yy, xx = np.mgrid[0:F, 0:F].astype(np.float64)
+    coef = [(2.0, 0.3, -0.7), (5.0, -1.25, 0.5)]
+    I_cam = np.stack([c0 + c1 * yy + c2 * xx for c0, c1, c2 in coef])
+    out, mask = orc.tilt_correct(I_cam, z, p, alpha)
+    y, x, _ = orc.tilt_camera_index(F, z, p, alpha, yy, xx)
+    assert mask.any() and not mask.all()
+    for j, (c0, c1, c2) in enumerate(coef):
+        m = mask[j]
+        assert np.abs(out[j][m] - (c0 + c1 * y[m] + c2 * x[m])).max() < 1e-12
+        assert (out[j][~m] == 0).all()
+    # the mask is the set of model pixels whose taps lie inside the crop
+    inside = (y >= 0) & (y < F - 1) & (x >= 0) & (x < F - 1)
+    assert (mask[0] == inside).all() and (mask[1] == inside).all()
+
+
+def test_tilt_correction_without_tilt_is_near_identity():
+    F = 64
+    yy, xx = np.mgrid[0:F, 0:F].astype(np.float64)
+    y, x, ok = orc.tilt_camera_index(F, 88e-3, 15e-6, 0.0, yy, xx)
+    assert ok.all()
+    assert np.abs(y - yy).max() < 1e-3 and np.abs(x - xx).max() < 1e-3
+    I = np.exp(-((yy - 30) ** 2 + (xx - 34) ** 2) / 200.0)[None]
+    out, mask = orc.tilt_correct(I, 88e-3, 15e-6, 0.0)
+    inner = np.zeros((F, F), bool)
+    inner[1:F - 1, 1:F - 1] = True
+    assert mask[0][inner].all()
+    assert np.abs(out[0] - I[0])[inner].max() < 1e-4
+
+
+def test_tilt_correction_masks_the_model_pixels_that_touch_a_rejected_camera_pixel():
+    """A camera pixel outside [lo, hi) removes exactly the model pixels whose bilinear
+    footprint (floor(y)..floor(y)+1, floor(x)..floor(x)+1) contains it."""
+    F, z, p, alpha = 64, 0.02, 15e-6, math.radians(70)
+    I_cam = np.full((2, F, F), 10.0)
+    I_cam[0, 30, 41] = 65535.0          # saturated (the upper threshold itself is rejected)
+    I_cam[1, 12, 7] = 1.0               # below the noise threshold (< lo)
+    I_cam[1, 40, 20] = 4.0              # the lower threshold itself is kept
+    out, mask = orc.tilt_correct(I_cam, z, p, alpha, lo=4.0, hi=65535.0)
+    yy, xx = np.mgrid[0:F, 0:F].astype(np.float64)
+    y, x, _ = orc.tilt_camera_index(F, z, p, alpha, yy, xx)
+    inside = (y >= 0) & (y < F - 1) & (x >= 0) & (x < F - 1)
+    fy, fx = np.floor(np.where(inside, y, -9)), np.floor(np.where(inside, x, -9))
+    for j, (cy, cx) in enumerate([(30, 41), (12, 7)]):
+        touches = inside & ((fy == cy) | (fy == cy - 1)) & ((fx == cx) | (fx == cx - 1))
+        assert touches.any()
+        assert (mask[j] == (inside & ~touches)).all()
+        if j == 0:
+            assert np.abs(out[j][mask[j]] - 10.0).max() < 1e-12
+
+
+def test_tilt_correction_undoes_the_in_model_remap_of_smooth_patterns():
+    """Remap a smooth model-grid pattern to the camera (remap_apply) and correct it back:
+    the result is the pattern again, to the error of two bilinear interpolations."""
+    F, z, p, alpha = 64, 0.02, 15e-6, math.radians(70)
+    taps = orc.remap_taps(F, z, p, alpha)
+    yy, xx = np.mgrid[0:F, 0:F].astype(np.float64)
+    I = 1.0 + np.exp(-((yy - 33) ** 2 / 300.0 + (xx - 29) ** 2 / 150.0))
+    cam = orc.remap_apply(I, taps)
+    out, mask = orc.tilt_correct(cam[None], z, p, alpha)
+    y, x, _ = orc.tilt_camera_index(F, z, p, alpha, yy, xx)
+    # model pixels whose four camera taps all received a value from the remap
+    y0 = np.clip(np.floor(y), 0, F - 2).astype(int)
+    x0 = np.clip(np.floor(x), 0, F - 2).astype(int)
+    v = taps.valid
+    full = mask[0] & v[y0, x0] & v[y0 + 1, x0] & v[y0, x0 + 1] & v[y0 + 1, x0 + 1]
+    assert full.sum() > F * F // 2
+    assert np.abs(out[0] - I)[full].max() < 5e-3
+
+
+# ----------------------------------------------------------------------------
 # Adam
 # ----------------------------------------------------------------------------
 
