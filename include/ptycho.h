@@ -387,6 +387,38 @@ int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J, const int
                            const int32_t* obj_w, const int32_t* pos, const float* O, const float* P,
                            const float* sigma, const float* bg, float* I_pred, void* stream);
 
+/* Data-side tilt correction: the tilted-plane remap of the measurement model (f5 of Eq. 2)
+ * applied once to the measured patterns instead of inside the model, the way the paper
+ * preprocesses its reflection data (Section "Experimental setup and ptychography
+ * reconstruction": each pattern is interpolated non-uniformly onto a grid uniform in
+ * sample-plane spatial frequency, the correction yields the mask of the reduced field of
+ * view, and pixels outside the value thresholds are discarded).  The corrected patterns are
+ * fitted by a plan built with remap = 0, passing the mask with mask_per_frame = 1.
+ * The model grid is that of the in-model remap: F x F, zero frequency at (F/2, F/2),
+ * spacings db = (p/z) cos(tilt) along rows and da = p/z along columns in the reflected
+ * ray's in-plane direction cosines.  Model pixel (i, k) has b = (i - F/2) db and
+ * a = (k - F/2) da; rotated by the tilt about the camera x axis its ray is (a, b + sin, w),
+ * w = sqrt(1 - a^2 - (b + sin)^2) >= 0 (it leaves the sample surface), so in the camera frame
+ * d_y = (b + sin) cos - w sin and d_z = (b + sin) sin + w cos, and it meets the camera at
+ * X = z a / d_z, Y = z d_y / d_z: fractional camera index (Y/p + F/2, X/p + F/2), evaluated in
+ * FP64 with every operation rounded separately.  The output is the bilinear interpolation of
+ * the camera pattern there.  A model pixel is kept (mask 1) when the ray exists (w^2 > 0,
+ * d_z > 0), its four camera taps lie inside the crop (0 <= y < F-1, 0 <= x < F-1) and every
+ * tap value v satisfies lo <= v < hi (the paper's thresholds are 4 and 65535; pass -INFINITY
+ * and INFINITY for the field-of-view mask alone).
+ *   F          side of the camera crop and of the model grid, 2..8192
+ *   J          number of patterns; 0 launches nothing
+ *   z, det_pixel, tilt_rad   distance to the camera (m), camera pixel pitch (m) and tilt from
+ *              the sample normal (|tilt| < pi/2), as in ptycho_geom_t
+ *   I_cam      DEVICE [J][F][F] float, camera-grid patterns, zero frequency at (F/2, F/2)
+ *   I_model    DEVICE [J][F][F] float, out: corrected patterns, 0 where the mask is 0; must
+ *              not overlap I_cam
+ *   mask       DEVICE [J][F][F] uint8, out, or NULL: 1 = kept, 0 = not kept
+ * Asynchronous on stream.  PTYCHO_EINVAL for a bad size, geometry or threshold pair (NaN or
+ * lo >= hi), a NULL array with J > 0, or overlapping input and output. */
+int ptycho_tilt_correct(int32_t F, int64_t J, double z, double det_pixel, double tilt_rad, const float* I_cam,
+                        float lo, float hi, float* I_model, uint8_t* mask, void* stream);
+
 /* Static text for a return code. */
 const char* ptycho_strerror(int code);
 

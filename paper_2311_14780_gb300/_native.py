@@ -83,6 +83,8 @@ SIGNATURES = [
     ("ptycho_server_site_status", _I, [_VP, ctypes.c_int32, c_int32_p, c_double_p]),
     ("ptycho_server_release", _I, [_VP, ctypes.c_int32]),
     ("ptycho_server_used_bytes", ctypes.c_int64, [_VP]),
+    ("ptycho_tilt_correct", _I, [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 _VP, ctypes.c_float, ctypes.c_float, _VP, _VP, _VP]),
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 

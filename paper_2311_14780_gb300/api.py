@@ -8,6 +8,7 @@ ptycho_loss, ptycho_adjoint, ptycho_step).
 from __future__ import annotations
 
 import ctypes
+import math
 from typing import Optional, Sequence
 
 import numpy as np
@@ -360,6 +361,27 @@ class AdamState:
             t = getattr(self, name)
             setattr(s, name, None if t is None else t.data_ptr())
         return s
+
+
+def tilt_correct(I_cam: torch.Tensor, z: float, det_pixel: float, tilt_rad: float, lo: float = -math.inf,
+                 hi: float = math.inf, with_mask: bool = True, stream: Optional[torch.cuda.Stream] = None):
+    """Data-side tilt correction (``ptycho_tilt_correct``): camera patterns [J][F][F] (or one
+    [F][F]) float32 on the GPU -> (model-grid patterns, uint8 mask or None), ready for a plan
+    built with ``remap=False`` and the mask passed per frame."""
+    if I_cam.dim() == 2:
+        I_cam = I_cam.unsqueeze(0)
+    if I_cam.dim() != 3 or I_cam.shape[1] != I_cam.shape[2]:
+        raise ValueError("I_cam must be [J][F][F]")
+    if not I_cam.is_cuda or I_cam.dtype != torch.float32:
+        raise ValueError("I_cam must be a float32 CUDA tensor")
+    I_cam = I_cam.contiguous()
+    out = torch.empty_like(I_cam)
+    mask = torch.empty(I_cam.shape, dtype=torch.uint8, device=I_cam.device) if with_mask else None
+    rc = _native.lib().ptycho_tilt_correct(int(I_cam.shape[1]), int(I_cam.shape[0]), float(z), float(det_pixel),
+                                           float(tilt_rad), _ptr(I_cam), float(lo), float(hi), _ptr(out),
+                                           _ptr(mask), _stream_handle(stream))
+    _check(rc, "ptycho_tilt_correct")
+    return out, mask
 
 
 def plan_geometry_plan(r, **kw) -> Plan:

@@ -27,7 +27,7 @@ except Exception:  # pragma: no cover
 __all__ = [
     "Geometry", "Workload", "smooth_noise", "zernike_noll", "zernike_phase",
     "gaussian_amplitude", "probe_modes", "elliptical_aperture_modes",
-    "object_smooth", "object_rectangles", "raster_positions", "scale_positions",
+    "object_smooth", "object_rectangles", "raster_positions", "scale_positions", "camera_frames",
     "round_half_away", "poisson_measure", "default_eps", "config1", "config2", "near_truth",
     "serving_workload", "serving_request_inputs", "TextureBank",
     "config3", "config4", "config5_requests", "tiny_workload", "CONFIG3_GRID",
@@ -282,6 +282,23 @@ def poisson_measure(I_clean: np.ndarray, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     lam = np.clip(np.asarray(I_clean, dtype=np.float64), 0.0, None)
     return rng.poisson(lam).astype(np.float32)
+
+
+def camera_frames(J: int, F: int, seed: int, photons: float = 1e6, full_well: float = 65535.0) -> np.ndarray:
+    """Raw camera patterns [J][F][F] float32 shaped like the experiment's (zero frequency at
+    (F/2, F/2), a bright specular peak over a smooth speckle halo, Poisson photon noise) and
+    clipped at a 16-bit full well, so that the brightest pixels saturate and the dark halo
+    has pixels below a noise threshold of a few counts.  Inputs for the data-side tilt
+    correction; no part of the measurement model is evaluated here."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:F, 0:F].astype(np.float64) - F / 2
+    out = np.empty((J, F, F), np.float32)
+    for j in range(J):
+        peak = np.exp(-(yy ** 2 + xx ** 2) / 2.0)
+        halo = smooth_noise(rng, (F, F), max(1.0, F / 32)) * np.exp(-np.hypot(yy, xx) / (0.25 * F))
+        I = photons * (0.7 * peak / peak.sum() + 0.3 * halo / max(halo.sum(), 1e-300))
+        out[j] = np.minimum(rng.poisson(I), full_well).astype(np.float32)
+    return out
 
 
 def default_eps(I_meas: np.ndarray) -> float:

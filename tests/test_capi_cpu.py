@@ -1,6 +1,7 @@
 """Boundary checks that need no GPU: the library builds, loads, exports every symbol that
 ``include/ptycho.h`` declares, and rejects bad arguments on the host before any launch."""
 import ctypes
+import math
 import os
 import re
 
@@ -97,6 +98,26 @@ def test_null_arguments_are_rejected(lib):
     assert lib.ptycho_plan_create(None, ctypes.byref(h)) == -1
     assert lib.ptycho_forward(None, None, None, None, None, None, None) == -1
     assert lib.ptycho_plan_destroy(None) == 0
+
+
+def test_tilt_correct_rejects_bad_arguments_on_the_host(lib):
+    """Argument errors are caught before any CUDA call (so this runs without a GPU)."""
+    f = lib.ptycho_tilt_correct
+    a, b = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x100000)
+    ok = dict(F=64, J=3, z=0.02, p=15e-6, t=1.2, lo=-math.inf, hi=math.inf)
+
+    def call(**kw):
+        k = {**ok, **kw}
+        return f(k["F"], k["J"], k["z"], k["p"], k["t"], kw.get("cam", a), k["lo"], k["hi"], kw.get("out", b),
+                 None, None)
+
+    assert call(F=1) == -1 and call(F=9000) == -1 and call(J=-1) == -1
+    assert call(z=0.0) == -1 and call(p=-1e-6) == -1 and call(z=math.inf) == -1
+    assert call(t=math.pi / 2) == -1 and call(t=math.nan) == -1
+    assert call(lo=5.0, hi=5.0) == -1 and call(lo=math.nan) == -1 and call(hi=math.nan) == -1
+    assert call(cam=None) == -1 and call(out=None) == -1
+    assert call(out=ctypes.c_void_p(0x1000 + 64 * 64 * 4)) == -1          # output overlaps the input
+    assert call(J=0, cam=None, out=None) == 0                            # nothing to do, nothing launched
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
