@@ -414,10 +414,30 @@ int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J, const int
  *   I_model    DEVICE [J][F][F] float, out: corrected patterns, 0 where the mask is 0; must
  *              not overlap I_cam
  *   mask       DEVICE [J][F][F] uint8, out, or NULL: 1 = kept, 0 = not kept
- * Asynchronous on stream.  PTYCHO_EINVAL for a bad size, geometry or threshold pair (NaN or
- * lo >= hi), a NULL array with J > 0, or overlapping input and output. */
+ * Asynchronous on stream.  The camera positions are computed first (ptycho_tilt_table) into a
+ * table that this call allocates stream-ordered (cudaMallocAsync) and frees again; callers that
+ * correct many stacks with one geometry build the table once and call ptycho_tilt_apply.
+ * PTYCHO_EINVAL for a bad size, geometry or threshold pair (NaN or lo >= hi), a NULL array with
+ * J > 0, or overlapping inputs and outputs; PTYCHO_ENOMEM when the table cannot be allocated. */
 int ptycho_tilt_correct(int32_t F, int64_t J, double z, double det_pixel, double tilt_rad, const float* I_cam,
                         float lo, float hi, float* I_model, uint8_t* mask, void* stream);
+
+/* Bytes of the tilt-correction table of an F x F grid (20 per model pixel: four FP32 bilinear
+ * weights, then one int32 camera offset of the top-left tap, -1 for a pixel that is never
+ * kept), or -1 when F is outside 2..8192. */
+int64_t ptycho_tilt_table_bytes(int32_t F);
+
+/* Fills a caller-owned DEVICE table (ptycho_tilt_table_bytes(F) bytes, 16-byte aligned) with
+ * the camera position of every model pixel for this geometry, as ptycho_tilt_correct defines
+ * it.  Asynchronous on stream; PTYCHO_EINVAL for a bad size or geometry, a NULL or misaligned
+ * table. */
+int ptycho_tilt_table(int32_t F, double z, double det_pixel, double tilt_rad, void* table, void* stream);
+
+/* The interpolation and masking of ptycho_tilt_correct with a table from ptycho_tilt_table
+ * (same F); the result is identical to ptycho_tilt_correct's for that geometry.  Arguments and
+ * errors as for ptycho_tilt_correct; the outputs must not overlap the table. */
+int ptycho_tilt_apply(int32_t F, int64_t J, const void* table, const float* I_cam, float lo, float hi,
+                      float* I_model, uint8_t* mask, void* stream);
 
 /* Static text for a return code. */
 const char* ptycho_strerror(int code);

@@ -85,6 +85,10 @@ SIGNATURES = [
     ("ptycho_server_used_bytes", ctypes.c_int64, [_VP]),
     ("ptycho_tilt_correct", _I, [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  _VP, ctypes.c_float, ctypes.c_float, _VP, _VP, _VP]),
+    ("ptycho_tilt_table_bytes", ctypes.c_int64, [ctypes.c_int32]),
+    ("ptycho_tilt_table", _I, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP]),
+    ("ptycho_tilt_apply", _I, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, ctypes.c_float, ctypes.c_float, _VP, _VP,
+                               _VP]),
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 

@@ -368,6 +368,28 @@ def tilt_correct(I_cam: torch.Tensor, z: float, det_pixel: float, tilt_rad: floa
     """Data-side tilt correction (``ptycho_tilt_correct``): camera patterns [J][F][F] (or one
     [F][F]) float32 on the GPU -> (model-grid patterns, uint8 mask or None), ready for a plan
     built with ``remap=False`` and the mask passed per frame."""
+    I_cam, out, mask = _tilt_io(I_cam, with_mask)
+    rc = _native.lib().ptycho_tilt_correct(int(I_cam.shape[1]), int(I_cam.shape[0]), float(z), float(det_pixel),
+                                           float(tilt_rad), _ptr(I_cam), float(lo), float(hi), _ptr(out),
+                                           _ptr(mask), _stream_handle(stream))
+    _check(rc, "ptycho_tilt_correct")
+    return out, mask
+
+
+def tilt_table(F: int, z: float, det_pixel: float, tilt_rad: float, device="cuda",
+               stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """Camera positions of the model pixels for one geometry (``ptycho_tilt_table``): a device
+    byte tensor to pass to :func:`tilt_apply` for every stack of patterns of that geometry."""
+    n = int(_native.lib().ptycho_tilt_table_bytes(int(F)))
+    if n < 0:
+        raise ValueError("F must be in 2..8192")
+    table = torch.empty(n, dtype=torch.uint8, device=device)
+    _check(_native.lib().ptycho_tilt_table(int(F), float(z), float(det_pixel), float(tilt_rad), _ptr(table),
+                                           _stream_handle(stream)), "ptycho_tilt_table")
+    return table
+
+
+def _tilt_io(I_cam: torch.Tensor, with_mask: bool):
     if I_cam.dim() == 2:
         I_cam = I_cam.unsqueeze(0)
     if I_cam.dim() != 3 or I_cam.shape[1] != I_cam.shape[2]:
@@ -377,10 +399,16 @@ def tilt_correct(I_cam: torch.Tensor, z: float, det_pixel: float, tilt_rad: floa
     I_cam = I_cam.contiguous()
     out = torch.empty_like(I_cam)
     mask = torch.empty(I_cam.shape, dtype=torch.uint8, device=I_cam.device) if with_mask else None
-    rc = _native.lib().ptycho_tilt_correct(int(I_cam.shape[1]), int(I_cam.shape[0]), float(z), float(det_pixel),
-                                           float(tilt_rad), _ptr(I_cam), float(lo), float(hi), _ptr(out),
-                                           _ptr(mask), _stream_handle(stream))
-    _check(rc, "ptycho_tilt_correct")
+    return I_cam, out, mask
+
+
+def tilt_apply(table: torch.Tensor, I_cam: torch.Tensor, lo: float = -math.inf, hi: float = math.inf,
+               with_mask: bool = True, stream: Optional[torch.cuda.Stream] = None):
+    """``ptycho_tilt_apply``: the tilt correction of a stack with a table from :func:`tilt_table`."""
+    I_cam, out, mask = _tilt_io(I_cam, with_mask)
+    rc = _native.lib().ptycho_tilt_apply(int(I_cam.shape[1]), int(I_cam.shape[0]), _ptr(table), _ptr(I_cam),
+                                         float(lo), float(hi), _ptr(out), _ptr(mask), _stream_handle(stream))
+    _check(rc, "ptycho_tilt_apply")
     return out, mask
 
 

@@ -118,6 +118,19 @@ def test_tilt_correct_rejects_bad_arguments_on_the_host(lib):
     assert call(cam=None) == -1 and call(out=None) == -1
     assert call(out=ctypes.c_void_p(0x1000 + 64 * 64 * 4)) == -1          # output overlaps the input
     assert call(J=0, cam=None, out=None) == 0                            # nothing to do, nothing launched
+    # the table / apply split
+    assert lib.ptycho_tilt_table_bytes(256) == 256 * 256 * 20 and lib.ptycho_tilt_table_bytes(1) == -1
+    assert lib.ptycho_tilt_table(64, 0.02, 15e-6, 1.2, None, None) == -1
+    assert lib.ptycho_tilt_table(64, 0.02, 15e-6, 1.2, ctypes.c_void_p(0x1008), None) == -1   # misaligned
+    assert lib.ptycho_tilt_table(64, -0.02, 15e-6, 1.2, a, None) == -1
+    tab = ctypes.c_void_p(0x200000)
+    ap = lib.ptycho_tilt_apply
+    assert ap(64, 3, None, a, -math.inf, math.inf, b, None, None) == -1
+    assert ap(64, 3, ctypes.c_void_p(0x200008), a, -math.inf, math.inf, b, None, None) == -1
+    assert ap(64, 3, tab, a, 2.0, 1.0, b, None, None) == -1
+    assert ap(64, 3, tab, a, -math.inf, math.inf, ctypes.c_void_p(0x200000 + 64), None, None) == -1  # out on the table
+    assert ap(64, 3, tab, a, -math.inf, math.inf, b, ctypes.c_void_p(0x100010), None) == -1        # mask on out
+    assert ap(64, 0, None, None, -math.inf, math.inf, None, None, None) == 0
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -81,6 +81,22 @@ def test_tilt_correct_full_size_camera_stack_sampled_frames(dev):
         check(I_cam[j:j + 1], out[j:j + 1], mask[j:j + 1], Z, syn.PAPER_TILT, 4.0, 65535.0)
 
 
+def test_tilt_table_and_apply_match_the_one_shot_correction(dev):
+    """A table built once serves several stacks (different J, ragged chunks) and gives the
+    one-shot call's result bit for bit."""
+    from paper_2311_14780_gb300 import tilt_apply, tilt_correct, tilt_table
+    F, z, t = 128, 0.05, syn.PAPER_TILT
+    table = tilt_table(F, z, P, t, device=dev)
+    for J, seed in ((1, 1), (17, 2), (40, 3)):
+        I_cam = torch.as_tensor(syn.camera_frames(J, F, seed=seed), device=dev)
+        a_out, a_mask = tilt_apply(table, I_cam, 4.0, 65535.0)
+        c_out, c_mask = tilt_correct(I_cam, z, P, t, 4.0, 65535.0)
+        torch.cuda.synchronize()
+        assert torch.equal(a_out, c_out) and torch.equal(a_mask, c_mask)
+    ref, mref = orc.tilt_correct(I_cam.cpu().numpy()[-3:], z, P, t, 4.0, 65535.0)
+    assert (a_mask.cpu().numpy()[-3:].astype(bool) == mref).all()
+
+
 def test_tilt_correct_without_mask_and_empty_stack(dev):
     from paper_2311_14780_gb300 import tilt_correct
     I_cam = syn.camera_frames(3, 64, seed=9)
