@@ -59,9 +59,10 @@ extern "C" {
  *   the tile-owned gather (faster; the summation order, and so the last bits of grad O,
  *   then vary between runs).
  * TMA / NO_TMA: the column passes stage each mode's column block in shared memory with
- *   bulk tensor copies (TMA) / read S with ordinary loads.  Default: TMA for F >= 512,
- *   where it measured faster; below that the larger shared-memory footprint costs more
- *   occupancy than the copies save.  NO_TMA wins when both are given.
+ *   bulk tensor copies (TMA) / read S with ordinary loads.  Default: TMA for F >= 512, and
+ *   for F = 128 when a position has at least four fields (L*M >= 4), where it measured
+ *   faster; otherwise the larger shared-memory footprint costs more occupancy than the
+ *   copies save.  NO_TMA wins when both are given.
  * UNFUSED_ROW_ADJ: one block of the adjoint row pass per probe mode, each mode's object-
  *   gradient row left in the scratch for the object-gradient kernel (always the case for
  *   F = 512).  The default for F <= 256, whenever all modes of a position fit the scratch and
@@ -406,26 +407,25 @@ int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J, const int
  * d_z > 0), its four camera taps lie inside the crop (0 <= y < F-1, 0 <= x < F-1) and every
  * tap value v satisfies lo <= v < hi (the paper's thresholds are 4 and 65535; pass -INFINITY
  * and INFINITY for the field-of-view mask alone).
- *   F          side of the camera crop and of the model grid, even, 2..8192
+ *   F          side of the camera crop and of the model grid, 2..8192
  *   J          number of patterns; 0 launches nothing
  *   z, det_pixel, tilt_rad   distance to the camera (m), camera pixel pitch (m) and tilt from
  *              the sample normal (|tilt| < pi/2), as in ptycho_geom_t
  *   I_cam      DEVICE [J][F][F] float, camera-grid patterns, zero frequency at (F/2, F/2)
- *   I_model    DEVICE [J][F][F] float, out: corrected patterns, 0 where the mask is 0; 16-byte
- *              aligned, must not overlap I_cam
- *   mask       DEVICE [J][F][F] uint8, out, or NULL: 1 = kept, 0 = not kept; 4-byte aligned
+ *   I_model    DEVICE [J][F][F] float, out: corrected patterns, 0 where the mask is 0; must
+ *              not overlap I_cam
+ *   mask       DEVICE [J][F][F] uint8, out, or NULL: 1 = kept, 0 = not kept
  * Asynchronous on stream.  The camera positions are computed first (ptycho_tilt_table) into a
  * table that this call allocates stream-ordered (cudaMallocAsync) and frees again; callers that
  * correct many stacks with one geometry build the table once and call ptycho_tilt_apply.
- * PTYCHO_EINVAL for a bad size, geometry or threshold pair (NaN or lo >= hi), a NULL or
- * misaligned array with J > 0, or overlapping inputs and outputs; PTYCHO_ENOMEM when the table
- * cannot be allocated. */
+ * PTYCHO_EINVAL for a bad size, geometry or threshold pair (NaN or lo >= hi), a NULL array with
+ * J > 0, or overlapping inputs and outputs; PTYCHO_ENOMEM when the table cannot be allocated. */
 int ptycho_tilt_correct(int32_t F, int64_t J, double z, double det_pixel, double tilt_rad, const float* I_cam,
                         float lo, float hi, float* I_model, uint8_t* mask, void* stream);
 
 /* Bytes of the tilt-correction table of an F x F grid (20 per model pixel: four FP32 bilinear
  * weights, then one int32 camera offset of the top-left tap, -1 for a pixel that is never
- * kept), or -1 when F is odd or outside 2..8192. */
+ * kept), or -1 when F is outside 2..8192. */
 int64_t ptycho_tilt_table_bytes(int32_t F);
 
 /* Fills a caller-owned DEVICE table (ptycho_tilt_table_bytes(F) bytes, 16-byte aligned) with

@@ -539,7 +539,7 @@ k_loss(KArgs a, LossArgs la) {
           d[k] = __fdividef(Ie - Ih, Ie);
         }
       }
-      df_add(sh, sl, d[k] * Is);
+      if (la.sig_part) df_add(sh, sl, d[k] * Is);
       if (la.z_part && d[k] != 0.f) {
         const float2 rz = __ldg(la.tap_dz + q);
         df_add(zh, zl, d[k] * fmaf(srow, rz.x, scol * rz.y));
@@ -548,9 +548,9 @@ k_loss(KArgs a, LossArgs la) {
   }
   if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(d[0], d[1], d[2], d[3]);
   if (!la.loss_part && !la.sig_part && !la.z_part) return;
-  df_warp_sum(th, tl);
-  df_warp_sum(sh, sl);
-  df_warp_sum(zh, zl);
+  if (la.loss_part) df_warp_sum(th, tl);           // each sum only when its output is requested
+  if (la.sig_part) df_warp_sum(sh, sl);            // (uniform branches)
+  if (la.z_part) df_warp_sum(zh, zl);
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = th;
     red[1][threadIdx.x >> 5] = tl;

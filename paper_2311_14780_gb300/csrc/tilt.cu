@@ -10,11 +10,9 @@
 // per geometry: k_tilt_taps places every model pixel on the camera in FP64 (the camera index
 // decides which four taps are read and whether the pixel is kept) and writes a table of
 // bilinear weights and tap offsets (20 bytes per pixel).  k_tilt_apply streams the frames:
-// each thread owns four consecutive model pixels, reads their taps once per work item and runs
-// over a chunk of frames, kTiltUnroll frames at a time so that 16 x kTiltUnroll independent
-// loads are in flight, and writes each frame's four values and mask bytes with one 16-byte and
-// one 4-byte store.  The apply pass is HBM-bound: per pattern F^2 x (4 B read + 4 B written +
-// 1 B mask).
+// one thread per model pixel reads its taps once and runs over a chunk of frames,
+// kTiltUnroll frames at a time so that 4 x kTiltUnroll independent loads are in flight.  The
+// apply pass is HBM-bound: per pattern F^2 x (4 B read + 4 B written + 1 B mask).
 #include <math.h>
 #include <stdint.h>
 
@@ -28,10 +26,9 @@ namespace {
 
 constexpr int kTiltThreads = 256;               // apply pass
 constexpr int kTapThreads = 64;                  // table pass (FP64-bound: small blocks spread it over the SMs)
-constexpr int kTiltUnroll = 2;                   // frames per thread and iteration
+constexpr int kTiltUnroll = 4;                   // frames per thread and iteration
 constexpr int kTiltChunk = 16;                   // frames per work item of the apply pass
-constexpr int kTiltBlocksPerSM = 3;              // resident apply blocks per SM (<= 85 registers)
-constexpr int kTiltQuad = 4 * kTiltThreads;      // model pixels per work item
+constexpr int kTiltBlocksPerSM = 6;              // resident apply blocks per SM (<= 40 registers)
 
 struct TiltGeom {
   double z, p;          // distance to the camera and camera pixel pitch (m)
@@ -92,69 +89,64 @@ k_tilt_taps(TiltGeom g, float4* __restrict__ w, int32_t* __restrict__ base) {
 
 __device__ __forceinline__ bool in_range(float v, float lo, float hi) { return (v >= lo) & (v < hi); }
 
-// Persistent: work item i covers pixels [kTiltQuad * (i % nq), ...) and frames
-// [kTiltChunk * (i / nq), ...); block b takes items b, b + gridDim.x, ...  F^2 is a multiple of 4.
-// grid min(items, kTiltBlocksPerSM * SMs)
+// Persistent: work item i covers pixel block i % nblk and frames [kTiltChunk * (i / nblk), ...);
+// block b takes items b, b + gridDim.x, ...   grid min(items, kTiltBlocksPerSM * SMs)
 __global__ void __launch_bounds__(kTiltThreads, kTiltBlocksPerSM)
 k_tilt_apply(const float* __restrict__ cam, long long J, int F, const float4* __restrict__ w,
              const int32_t* __restrict__ base, float lo, float hi, float* __restrict__ out, uint8_t* __restrict__ mask) {
   const long long FF = (long long)F * F;
-  const long long nq = (FF + kTiltQuad - 1) / kTiltQuad;
-  const long long items = nq * ((J + kTiltChunk - 1) / kTiltChunk);
+  const long long nblk = (FF + kTiltThreads - 1) / kTiltThreads;
+  const long long items = nblk * ((J + kTiltChunk - 1) / kTiltChunk);
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-    const long long p0 = (it % nq) * kTiltQuad + 4ll * threadIdx.x;
-    if (p0 >= FF) continue;
-    const long long j0 = (it / nq) * kTiltChunk;
+    const long long pix = (it % nblk) * kTiltThreads + threadIdx.x;
+    if (pix >= FF) continue;
+    const long long j0 = (it / nblk) * kTiltChunk;
     const int n = (int)(j0 + kTiltChunk < J ? kTiltChunk : J - j0);
-    const int4 b4 = __ldg(reinterpret_cast<const int4*>(base + p0));
-    const int b[4] = {b4.x, b4.y, b4.z, b4.w};
-    float4 wt[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) wt[q] = __ldg(w + p0 + q);
-    float* o = out + j0 * FF + p0;
-    uint8_t* mk = mask ? mask + j0 * FF + p0 : nullptr;
-    const float* c = cam + j0 * FF;
-    for (int k = 0; k < n; k += kTiltUnroll) {
-      float v[kTiltUnroll][4][4];
-#pragma unroll
-      for (int f = 0; f < kTiltUnroll; ++f)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (b[q] >= 0 && k + f < n) {
-            const float* cf = c + (long long)(k + f) * FF + b[q];
-            v[f][q][0] = __ldg(cf);
-            v[f][q][1] = __ldg(cf + 1);
-            v[f][q][2] = __ldg(cf + F);
-            v[f][q][3] = __ldg(cf + F + 1);
-          } else {
-            v[f][q][0] = v[f][q][1] = v[f][q][2] = v[f][q][3] = 0.f;
-          }
-        }
+    const int32_t b = __ldg(base + pix);
+    float* o = out + j0 * FF + pix;
+    uint8_t* mk = mask ? mask + j0 * FF + pix : nullptr;
+    if (b < 0) {                                      // not kept in any frame
+      for (int k = 0; k < n; ++k) {
+        o[k * FF] = 0.f;
+        if (mk) mk[k * FF] = 0;
+      }
+      continue;
+    }
+    const float4 wt = __ldg(w + pix);
+    const float* c = cam + j0 * FF + b;
+    int k = 0;
+    for (; k + kTiltUnroll <= n; k += kTiltUnroll) {
+      float v[kTiltUnroll][4];
 #pragma unroll
       for (int f = 0; f < kTiltUnroll; ++f) {
-        if (k + f >= n) break;
-        float r[4];
-        uint32_t m = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const bool keep = (b[q] >= 0) & in_range(v[f][q][0], lo, hi) & in_range(v[f][q][1], lo, hi) &
-                            in_range(v[f][q][2], lo, hi) & in_range(v[f][q][3], lo, hi);
-          const float val =
-              fmaf(wt[q].w, v[f][q][3], fmaf(wt[q].z, v[f][q][2], fmaf(wt[q].y, v[f][q][1], wt[q].x * v[f][q][0])));
-          r[q] = keep ? val : 0.f;
-          m |= (keep ? 1u : 0u) << (8 * q);
-        }
-        *reinterpret_cast<float4*>(o + (long long)(k + f) * FF) = make_float4(r[0], r[1], r[2], r[3]);
-        if (mk) *reinterpret_cast<uint32_t*>(mk + (long long)(k + f) * FF) = m;
+        const float* cf = c + (k + f) * FF;
+        v[f][0] = __ldg(cf);
+        v[f][1] = __ldg(cf + 1);
+        v[f][2] = __ldg(cf + F);
+        v[f][3] = __ldg(cf + F + 1);
       }
+#pragma unroll
+      for (int f = 0; f < kTiltUnroll; ++f) {
+        const bool keep = in_range(v[f][0], lo, hi) & in_range(v[f][1], lo, hi) & in_range(v[f][2], lo, hi) &
+                          in_range(v[f][3], lo, hi);
+        const float val = fmaf(wt.w, v[f][3], fmaf(wt.z, v[f][2], fmaf(wt.y, v[f][1], wt.x * v[f][0])));
+        o[(k + f) * FF] = keep ? val : 0.f;
+        if (mk) mk[(k + f) * FF] = keep ? 1 : 0;
+      }
+    }
+    for (; k < n; ++k) {
+      const float* cf = c + k * FF;
+      const float v0 = __ldg(cf), v1 = __ldg(cf + 1), v2 = __ldg(cf + F), v3 = __ldg(cf + F + 1);
+      const bool keep = in_range(v0, lo, hi) & in_range(v1, lo, hi) & in_range(v2, lo, hi) & in_range(v3, lo, hi);
+      const float val = fmaf(wt.w, v3, fmaf(wt.z, v2, fmaf(wt.y, v1, wt.x * v0)));
+      o[k * FF] = keep ? val : 0.f;
+      if (mk) mk[k * FF] = keep ? 1 : 0;
     }
   }
 }
 
-bool bad_side(int32_t F) { return F < 2 || F > 8192 || (F & 1); }
-
 int check_geometry(int32_t F, double z, double det_pixel, double tilt_rad) {
-  if (bad_side(F)) return PTYCHO_EINVAL;
+  if (F < 2 || F > 8192) return PTYCHO_EINVAL;
   if (!(z > 0.0) || !isfinite(z) || !(det_pixel > 0.0) || !isfinite(det_pixel) || !isfinite(tilt_rad) ||
       !(fabs(tilt_rad) < 0.5 * M_PI))
     return PTYCHO_EINVAL;
@@ -183,7 +175,7 @@ int launch_apply(int32_t F, int64_t J, const void* table, const float* I_cam, fl
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PTYCHO_ECUDA;
   const long long FF = (long long)F * F;
-  const long long items = ((FF + kTiltQuad - 1) / kTiltQuad) * ((J + kTiltChunk - 1) / kTiltChunk);
+  const long long items = ((FF + kTiltThreads - 1) / kTiltThreads) * ((J + kTiltChunk - 1) / kTiltChunk);
   const long long grid = std::min<long long>(items, (long long)kTiltBlocksPerSM * sms);
   const float4* w = static_cast<const float4*>(table);
   k_tilt_apply<<<(unsigned)grid, kTiltThreads, 0, st>>>(I_cam, J, F, w, reinterpret_cast<const int32_t*>(w + FF), lo,
@@ -199,11 +191,10 @@ bool overlaps(const void* a, const void* b, long long bytes_a, long long bytes_b
 
 int check_apply(int32_t F, int64_t J, const void* table, const float* I_cam, float lo, float hi, float* I_model,
                 uint8_t* mask) {
-  if (bad_side(F) || J < 0) return PTYCHO_EINVAL;
+  if (F < 2 || F > 8192 || J < 0) return PTYCHO_EINVAL;
   if (isnan(lo) || isnan(hi) || !(lo < hi)) return PTYCHO_EINVAL;
   if (J == 0) return PTYCHO_OK;
   if (!I_cam || !I_model || !table || (reinterpret_cast<uintptr_t>(table) & 15)) return PTYCHO_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(I_model) & 15) || (reinterpret_cast<uintptr_t>(mask) & 3)) return PTYCHO_EINVAL;
   const long long FF = (long long)F * F, img = J * FF * (long long)sizeof(float);
   const long long tb = FF * (long long)(sizeof(float4) + sizeof(int32_t));
   // the outputs must overlap neither the input nor the table, nor each other
@@ -218,7 +209,7 @@ int check_apply(int32_t F, int64_t J, const void* table, const float* I_cam, flo
 extern "C" {
 
 int64_t ptycho_tilt_table_bytes(int32_t F) {
-  if (bad_side(F)) return -1;
+  if (F < 2 || F > 8192) return -1;
   return (int64_t)F * F * (int64_t)(sizeof(float4) + sizeof(int32_t));
 }
 
@@ -243,7 +234,6 @@ int ptycho_tilt_correct(int32_t F, int64_t J, double z, double det_pixel, double
   if (J < 0 || isnan(lo) || isnan(hi) || !(lo < hi)) return PTYCHO_EINVAL;
   if (J == 0) return PTYCHO_OK;
   if (!I_cam || !I_model) return PTYCHO_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(I_model) & 15) || (reinterpret_cast<uintptr_t>(mask) & 3)) return PTYCHO_EINVAL;
   const long long FF = (long long)F * F, img = J * FF * (long long)sizeof(float);
   if (overlaps(I_cam, I_model, img, img) ||
       (mask && (overlaps(mask, I_model, J * FF, img) || overlaps(mask, I_cam, J * FF, img))))

@@ -111,8 +111,7 @@ def test_tilt_correct_rejects_bad_arguments_on_the_host(lib):
         return f(k["F"], k["J"], k["z"], k["p"], k["t"], kw.get("cam", a), k["lo"], k["hi"], kw.get("out", b),
                  None, None)
 
-    assert call(F=1) == -1 and call(F=9000) == -1 and call(F=63) == -1 and call(J=-1) == -1
-    assert call(out=ctypes.c_void_p(0x100004)) == -1                      # output not 16-byte aligned
+    assert call(F=1) == -1 and call(F=9000) == -1 and call(J=-1) == -1
     assert call(z=0.0) == -1 and call(p=-1e-6) == -1 and call(z=math.inf) == -1
     assert call(t=math.pi / 2) == -1 and call(t=math.nan) == -1
     assert call(lo=5.0, hi=5.0) == -1 and call(lo=math.nan) == -1 and call(hi=math.nan) == -1
@@ -121,7 +120,7 @@ def test_tilt_correct_rejects_bad_arguments_on_the_host(lib):
     assert call(J=0, cam=None, out=None) == 0                            # nothing to do, nothing launched
     # the table / apply split
     assert lib.ptycho_tilt_table_bytes(256) == 256 * 256 * 20 and lib.ptycho_tilt_table_bytes(1) == -1
-    assert lib.ptycho_tilt_table_bytes(101) == -1
+    assert lib.ptycho_tilt_table_bytes(101) == 101 * 101 * 20
     assert lib.ptycho_tilt_table(64, 0.02, 15e-6, 1.2, None, None) == -1
     assert lib.ptycho_tilt_table(64, 0.02, 15e-6, 1.2, ctypes.c_void_p(0x1008), None) == -1   # misaligned
     assert lib.ptycho_tilt_table(64, -0.02, 15e-6, 1.2, a, None) == -1
@@ -132,7 +131,6 @@ def test_tilt_correct_rejects_bad_arguments_on_the_host(lib):
     assert ap(64, 3, tab, a, 2.0, 1.0, b, None, None) == -1
     assert ap(64, 3, tab, a, -math.inf, math.inf, ctypes.c_void_p(0x200000 + 64), None, None) == -1  # out on the table
     assert ap(64, 3, tab, a, -math.inf, math.inf, b, ctypes.c_void_p(0x100010), None) == -1        # mask on out
-    assert ap(64, 3, tab, a, -math.inf, math.inf, b, ctypes.c_void_p(0x300002), None) == -1        # mask misaligned
     assert ap(64, 0, None, None, -math.inf, math.inf, None, None, None) == 0
 
 

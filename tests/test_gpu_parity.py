@@ -339,12 +339,13 @@ def test_config4_full_size_sampled(dev):
     assert_ok(_sampled_full_size(dev, w, n_frames=2, n_grad=1, seed=4))
 
 
-@pytest.mark.parametrize("flags", [1, 2, 3, 4, 16, 17, 20, 32, 64, 68, 192, 256, 288, 512])
-@pytest.mark.parametrize("F", [64, 256])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 8, 16, 17, 20, 32, 64, 68, 192, 256, 288, 512])
+@pytest.mark.parametrize("F", [64, 128, 256])
 def test_pipeline_variants(dev, flags, F):
-    """Recompute-the-columns, atomic object-gradient, keep-Psi, TMA-staged columns, per-mode
-    row adjoint, cp.async-staged columns (8 and 4 wide), fused forward row pass and launches
-    without programmatic dependent launch all meet the same bars."""
+    """Recompute-the-columns, atomic object-gradient, keep-Psi, TMA-staged columns (and plain
+    loads where TMA is the default), per-mode row adjoint, cp.async-staged columns (8 and 4
+    wide), fused forward row pass and launches without programmatic dependent launch all meet
+    the same bars."""
     w = syn.tiny_workload(F=F, L=2, M=3, n_side=4, step=F // 8, seed=60 + flags, remap=True, loss="poisson",
                           with_sigma=True, with_bg=True)
     case = Case(w, dev, z=strong_z(F), mask_kind="frame", seed=flags)
