@@ -30,7 +30,7 @@ namespace ptycho {
 
 constexpr int kMaxL = 16;
 constexpr int kLossThreads = 256;
-constexpr int kLossPx = 4;       // camera pixels per thread in the loss kernel
+constexpr int kLossPx = 8;       // camera pixels per thread in the loss kernel (a multiple of 4)
 template <int F> __host__ __device__ constexpr int loss_blocks() { return F * F / (kLossThreads * kLossPx); }
 constexpr int kTile = 32;        // object-gradient tile side
 constexpr int kMaxB = 512;       // positions per batch (upper bound)
@@ -491,19 +491,25 @@ k_loss(KArgs a, LossArgs la) {
     if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * NB + blockIdx.x] = 0.0;
     if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * NB + blockIdx.x] = 0.0;
     if (la.z_part && threadIdx.x == 0) la.z_part[(long long)i * NB + blockIdx.x] = 0.0;
-    if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (la.D)
+#pragma unroll
+      for (int k = 0; k < kLossPx; k += 4)
+        *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0 + k) = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   const float* Ip = la.Ipart + (long long)b * a.G * FF;
   int tb[kLossPx];
   float2 tw[kLossPx];
   if (la.remap) {
-    const int4 t4 = *reinterpret_cast<const int4*>(la.tap_base + q0);
-    const float4 w01 = *reinterpret_cast<const float4*>(la.tap_w + q0);
-    const float4 w23 = *reinterpret_cast<const float4*>(la.tap_w + q0 + 2);
-    tb[0] = t4.x; tb[1] = t4.y; tb[2] = t4.z; tb[3] = t4.w;
-    tw[0] = make_float2(w01.x, w01.y); tw[1] = make_float2(w01.z, w01.w);
-    tw[2] = make_float2(w23.x, w23.y); tw[3] = make_float2(w23.z, w23.w);
+#pragma unroll
+    for (int k = 0; k < kLossPx; k += 4) {
+      const int4 t4 = *reinterpret_cast<const int4*>(la.tap_base + q0 + k);
+      const float4 w01 = *reinterpret_cast<const float4*>(la.tap_w + q0 + k);
+      const float4 w23 = *reinterpret_cast<const float4*>(la.tap_w + q0 + k + 2);
+      tb[k] = t4.x; tb[k + 1] = t4.y; tb[k + 2] = t4.z; tb[k + 3] = t4.w;
+      tw[k] = make_float2(w01.x, w01.y); tw[k + 1] = make_float2(w01.z, w01.w);
+      tw[k + 2] = make_float2(w23.x, w23.y); tw[k + 3] = make_float2(w23.z, w23.w);
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < kLossPx; ++k) { tb[k] = 0; tw[k] = make_float2(0.f, 0.f); }
@@ -546,7 +552,10 @@ k_loss(KArgs a, LossArgs la) {
       }
     }
   }
-  if (la.D) *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0) = make_float4(d[0], d[1], d[2], d[3]);
+  if (la.D)
+#pragma unroll
+    for (int k = 0; k < kLossPx; k += 4)
+      *reinterpret_cast<float4*>(la.D + (long long)b * FF + q0 + k) = make_float4(d[k], d[k + 1], d[k + 2], d[k + 3]);
   if (!la.loss_part && !la.sig_part && !la.z_part) return;
   if (la.loss_part) df_warp_sum(th, tl);           // each sum only when its output is requested
   if (la.sig_part) df_warp_sum(sh, sl);            // (uniform branches)
@@ -584,7 +593,7 @@ struct AdjArgs {
 
 // One thread per model pixel u and kRtPos positions of the batch: the CSR entries of u are
 // read once and the positions' D loads are independent.   grid (F*F/256, ceil(nb/kRtPos))
-constexpr int kRtPos = 4;
+constexpr int kRtPos = 8;
 template <int F>
 __global__ void __launch_bounds__(256)
 k_remap_adj(KArgs a, AdjArgs aa) {

@@ -28,7 +28,7 @@ constexpr int kTiltThreads = 256;               // apply pass
 constexpr int kTapThreads = 64;                  // table pass (FP64-bound: small blocks spread it over the SMs)
 constexpr int kTiltUnroll = 4;                   // frames per thread and iteration
 constexpr int kTiltChunk = 16;                   // frames per work item of the apply pass
-constexpr int kTiltBlocksPerSM = 6;              // resident apply blocks per SM (<= 40 registers)
+constexpr int kTiltBlocksPerSM = 4;              // resident apply blocks per SM (<= 64 registers)
 
 struct TiltGeom {
   double z, p;          // distance to the camera and camera pixel pitch (m)
