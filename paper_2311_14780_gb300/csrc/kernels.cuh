@@ -30,7 +30,7 @@ namespace ptycho {
 
 constexpr int kMaxL = 16;
 constexpr int kLossThreads = 256;
-constexpr int kLossPx = 8;       // camera pixels per thread in the loss kernel (a multiple of 4)
+constexpr int kLossPx = 4;       // camera pixels per thread in the loss kernel (a multiple of 4)
 template <int F> __host__ __device__ constexpr int loss_blocks() { return F * F / (kLossThreads * kLossPx); }
 constexpr int kTile = 32;        // object-gradient tile side
 constexpr int kMaxB = 512;       // positions per batch (upper bound)
