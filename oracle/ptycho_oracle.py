@@ -38,6 +38,8 @@ Readings of points where the paper is silent (each also recorded in the design n
   sum (I+eps) - Ihat - Ihat*log((I+eps)/Ihat) with 0*log(.) := 0; no normalisation;
   mixed Poisson-Gaussian with read-noise variance s2: the Poisson deviance of
   (I+eps+s2, max(Ihat+s2, 0)) (the shifted-Poisson approximation);
+* object regularisation (optional): L1 and total variation of the smoothed amplitude
+  sqrt(|O|^2 + eta^2), forward differences with none across the last row and column;
 * gradient convention g = dL/dRe + i dL/dIm (complex parameters);
 * Adam acts on real and imaginary parts as separate real parameters.
 
@@ -55,7 +57,9 @@ differences of the fractional model indices and of the loss with the remap rebui
 exactness for an intensity linear on the model grid, and zero rate at the specular pixel; for
 the data-side tilt correction: the inverse map undoes the forward map at every camera pixel,
 exactness for patterns affine on the camera, near-identity without tilt, the mask of a
-saturated pixel, and undoing the in-model remap of smooth patterns).  The tilted-plane remap formula itself is a reading of the
+saturated pixel, and undoing the in-model remap of smooth patterns; for the object regulariser:
+finite differences, the closed form of an object of constant amplitude and of a linear
+amplitude ramp, and invariance under a global phase).  The tilted-plane remap formula itself is a reading of the
 cited geometry and is only partially pinned (identity limit, constants, adjointness,
 the paper's NA and pixel-ratio figures).
 """
@@ -590,6 +594,35 @@ def gradient_z(O, P, pos, Imeas, kind, eps, taps, rates, sigma=None, bg=None, ma
 # ----------------------------------------------------------------------------
 # Adam (Kingma & Ba), real and imaginary parts as separate real parameters
 # ----------------------------------------------------------------------------
+
+def regulariser(O, mu_l1: float, mu_tv: float, eta: float):
+    """Object regularisation (the loss adapted by regularisers, Section "Universal Ptychography
+    Algorithm"; the paper names L1 and total-variation regularisation of the object amplitude in
+    Section "3D structure information characterisation"; the exact forms are in the missing
+    Supplementary Information).  Reading: with the smoothed amplitude a = sqrt(|O|^2 + eta^2) of
+    every pixel of every object O_l,
+        R = mu_l1 * sum a + mu_tv * sum sqrt(dx^2 + dy^2 + eta^2),
+    dx = a[r][c+1] - a[r][c] (0 in the last column), dy = a[r+1][c] - a[r][c] (0 in the last row).
+    Returns (R, [dR/dRe O_l + i dR/dIm O_l]); the gradient of a with respect to the real and
+    imaginary parts is O/a, so g = (dR/da) O / a."""
+    R = 0.0
+    grads = []
+    for O_l in O:
+        O_l = np.asarray(O_l, np.complex128)
+        a = np.sqrt(np.abs(O_l) ** 2 + eta * eta)
+        dx = np.zeros_like(a)
+        dy = np.zeros_like(a)
+        dx[:, :-1] = a[:, 1:] - a[:, :-1]
+        dy[:-1, :] = a[1:, :] - a[:-1, :]
+        t = np.sqrt(dx * dx + dy * dy + eta * eta)
+        R += mu_l1 * float(a.sum()) + mu_tv * float(t.sum())
+        px, py = dx / t, dy / t
+        dRda = np.full(a.shape, float(mu_l1)) - mu_tv * (px + py)   # through dx, dy of the pixel itself
+        dRda[:, 1:] += mu_tv * px[:, :-1]                           # through dx of the left neighbour
+        dRda[1:, :] += mu_tv * py[:-1, :]                           # through dy of the upper neighbour
+        grads.append(dRda * O_l / a)
+    return R, grads
+
 
 class AdamState:
     def __init__(self, shapes_O: List[tuple], shape_P: tuple):

@@ -532,6 +532,63 @@ def test_tilt_correction_undoes_the_in_model_remap_of_smooth_patterns():
 
 
 # ----------------------------------------------------------------------------
+# object regularisation (L1 and TV of the smoothed amplitude)
+# ----------------------------------------------------------------------------
+
+def test_regulariser_gradient_matches_central_finite_differences():
+    rng = np.random.default_rng(41)
+    O = [crandn(rng, 5, 7), crandn(rng, 4, 3)]
+    mu1, mutv, eta = 0.3, 0.7, 0.05
+    _, g = orc.regulariser(O, mu1, mutv, eta)
+    h = 1e-6
+    for l, (r, c) in [(0, (0, 0)), (0, (2, 3)), (0, (4, 6)), (0, (4, 0)), (1, (1, 2)), (1, (3, 2))]:
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            Op = [o.copy() for o in O]
+            Om = [o.copy() for o in O]
+            Op[l][r, c] += h * unit
+            Om[l][r, c] -= h * unit
+            fd = (orc.regulariser(Op, mu1, mutv, eta)[0] - orc.regulariser(Om, mu1, mutv, eta)[0]) / (2 * h)
+            an = g[l][r, c].real if part == "re" else g[l][r, c].imag
+            assert fd == pytest.approx(an, rel=1e-6, abs=1e-9), (l, r, c, part)
+
+
+def test_regulariser_of_a_constant_amplitude_object():
+    """|O| constant: every difference is 0, so TV = N eta and its gradient vanishes; the L1
+    part is N a with gradient mu_l1 O / a."""
+    rng = np.random.default_rng(42)
+    ph = rng.uniform(-np.pi, np.pi, size=(6, 9))
+    O = [0.8 * np.exp(1j * ph)]
+    mu1, mutv, eta = 0.4, 1.3, 0.02
+    R, g = orc.regulariser(O, mu1, mutv, eta)
+    a = math.sqrt(0.64 + eta * eta)
+    assert R == pytest.approx(54 * (mu1 * a + mutv * eta), rel=1e-13)
+    assert np.abs(g[0] - mu1 * O[0] / a).max() < 1e-13
+    R0, g0 = orc.regulariser(O, 0.0, mutv, eta)
+    assert np.abs(g0[0]).max() < 1e-13
+
+
+def test_regulariser_of_a_linear_amplitude_ramp():
+    """One row with amplitudes 0, s, 2s, ...: W-1 differences of s and one 0 at the end."""
+    W, s, eta = 8, 0.25, 1e-3
+    amp = s * np.arange(W, dtype=np.float64)
+    a = np.sqrt(amp ** 2 + eta ** 2)
+    O = [(amp * np.exp(0.3j))[None, :]]
+    R, _ = orc.regulariser(O, 0.0, 1.0, eta)
+    exp = float(np.sqrt(np.diff(a) ** 2 + eta ** 2).sum()) + eta
+    assert R == pytest.approx(exp, rel=1e-14)
+    assert R == pytest.approx((W - 1) * s, rel=1e-3)
+
+
+def test_regulariser_is_invariant_under_a_global_phase():
+    rng = np.random.default_rng(43)
+    O = [crandn(rng, 6, 5)]
+    R, g = orc.regulariser(O, 0.2, 0.9, 0.03)
+    Rr, gr = orc.regulariser([O[0] * np.exp(0.7j)], 0.2, 0.9, 0.03)
+    assert Rr == pytest.approx(R, rel=1e-13)
+    assert np.abs(gr[0] - g[0] * np.exp(0.7j)).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------
 # Adam
 # ----------------------------------------------------------------------------
 
