@@ -399,6 +399,8 @@ def run_ours(args, rank: int, world: int):
         plan.set_offsets(delta)
         st_pos = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2)
         pos_ms = timed(lambda: plan.step(st_pos, O2, P2, Im, loss_out=loss), args.corrections_steps)
+        st_reg = AdamState(plan, lr_O=1e-3, lr_P=1e-3, reg_l1=1e-2, reg_tv=1e-1, reg_eta=1e-3)
+        reg_ms = timed(lambda: plan.step(st_reg, O2, P2, Im, loss_out=loss), args.corrections_steps)
         st_all = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2, lr_sigma=1e-2, lr_bg=1e-2)
         all_ms = timed(lambda: plan.step(st_all, O2, P2, Im, sig, bgt, loss_out=loss), args.corrections_steps)
         z_ms = None
@@ -470,6 +472,9 @@ def run_ours(args, rank: int, world: int):
         corrections = {
             "steps": args.corrections_steps,
             "object_probe": {"ms_per_step": base_ms, "evals_per_s": evals / (base_ms / 1e3)},
+            "plus_regularisation": {"ms_per_step": reg_ms, "evals_per_s": evals / (reg_ms / 1e3),
+                                    "relative_time": reg_ms / base_ms,
+                                    "note": "L1 and TV of the object amplitude added in the step (ptycho_regularise)"},
             "plus_positions": {"ms_per_step": pos_ms, "evals_per_s": evals / (pos_ms / 1e3),
                                "relative_time": pos_ms / base_ms},
             "plus_positions_power_background": {"ms_per_step": all_ms, "evals_per_s": evals / (all_ms / 1e3),

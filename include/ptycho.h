@@ -163,6 +163,10 @@ typedef struct {
    * (see g_z of ptycho_adjoint_ex; requires the remap).  z itself lives in the plan's host
    * geometry: the caller updates it with ptycho_plan_set_distance. */
   double* g_z;
+  /* Optional object regularisation (see ptycho_regularise): reg_l1 > 0 or reg_tv > 0 adds the
+   * regulariser with smoothing reg_eta (> 0) to the loss and its gradient to the object's
+   * before Adam. */
+  float reg_l1, reg_tv, reg_eta;
 } ptycho_adam_t;
 
 /* Validates the geometry and every scan position (PTYCHO_ERANGE names an out-of-object
@@ -266,8 +270,24 @@ int ptycho_plan_set_distance(ptycho_plan_t* plan, double z);
  * the plain baseline (ptycho_plain_step) rejects plans with offsets. */
 int ptycho_plan_set_offsets(ptycho_plan_t* plan, float* delta);
 
+/* Object regularisation.  The paper adapts the loss with regularisers (Section "Universal
+ * Ptychography Algorithm") and names L1 and total-variation regularisation of the object
+ * amplitude (Section "3D structure information characterisation"); their exact forms are in its
+ * Supplementary Information, which is not available, so this is a reading.  With the smoothed
+ * amplitude a = sqrt(|O|^2 + eta^2) of every pixel of every object O_l,
+ *   R = mu_l1 sum a + mu_tv sum sqrt(dx^2 + dy^2 + eta^2),
+ *   dx = a[r][c+1] - a[r][c] (0 in the last column), dy = a[r+1][c] - a[r][c] (0 in the last row).
+ * Adds R to *loss_dev (DEVICE double, may be NULL) and g = dR/dRe + i dR/dIm = (dR/da) O / a to
+ * gO (packed objects, complex64, DEVICE), on stream.  mu_l1, mu_tv >= 0, eta > 0, all finite
+ * (PTYCHO_EINVAL otherwise); mu_l1 = mu_tv = 0 launches nothing.  Deterministic (each pixel has
+ * one owner; the value is summed in FP64 in a fixed order).  The first call allocates a small
+ * per-tile partial buffer in the plan (PTYCHO_ENOMEM if that fails). */
+int ptycho_regularise(ptycho_plan_t* plan, const float* O, float mu_l1, float mu_tv, float eta, float* gO,
+                      double* loss_dev, void* stream);
+
 /* One optimisation step on a batch of positions ("per batch" updates, Fig. 2 caption):
- * ptycho_adjoint into plan-owned gradient buffers, then Adam on O (lr_O) and P (lr_P) in
+ * ptycho_adjoint into plan-owned gradient buffers (plus the object regulariser when the state
+ * sets reg_l1 or reg_tv), then Adam on O (lr_O) and P (lr_P) in
  * place, and on sigma (lr_sigma > 0) and bg (lr_bg > 0) in place when the state asks for
  * it (sigma / bg must then be non-NULL; every component of sigma takes the Adam update,
  * with gradient 0 for positions outside the batch).  state->t is incremented on the host
@@ -359,7 +379,8 @@ int64_t ptycho_server_used_bytes(const ptycho_server_t* server);
 #define PTYCHO_K_ADAM 7          /* Adam update                                          */
 #define PTYCHO_K_REMAP_ADJ 8     /* R^T of the tilted-plane remap                         */
 #define PTYCHO_K_SHIFT 9         /* Fourier shift of fractional scan offsets + dL/ddelta  */
-#define PTYCHO_NUM_KERNELS 10
+#define PTYCHO_K_REG 10          /* object regulariser (value and gradient)               */
+#define PTYCHO_NUM_KERNELS 11
 int ptycho_plan_profile(ptycho_plan_t* plan, int enable);
 int ptycho_plan_profile_read(ptycho_plan_t* plan, double* ms, int64_t* launches);
 const char* ptycho_kernel_name(int kind);

@@ -39,6 +39,7 @@ class Adam(ctypes.Structure):
         ("v_bg", ctypes.c_void_p),
         ("lr_delta", ctypes.c_float), ("m_delta", ctypes.c_void_p), ("v_delta", ctypes.c_void_p),
         ("g_z", ctypes.c_void_p),
+        ("reg_l1", ctypes.c_float), ("reg_tv", ctypes.c_float), ("reg_eta", ctypes.c_float),
     ]
 
 
@@ -85,6 +86,7 @@ SIGNATURES = [
     ("ptycho_server_used_bytes", ctypes.c_int64, [_VP]),
     ("ptycho_tilt_correct", _I, [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  _VP, ctypes.c_float, ctypes.c_float, _VP, _VP, _VP]),
+    ("ptycho_regularise", _I, [_VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP, _VP, _VP]),
     ("ptycho_tilt_table_bytes", ctypes.c_int64, [ctypes.c_int32]),
     ("ptycho_tilt_table", _I, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _VP]),
     ("ptycho_tilt_apply", _I, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, ctypes.c_float, ctypes.c_float, _VP, _VP,
@@ -92,7 +94,7 @@ SIGNATURES = [
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 
-NUM_KERNELS = 10
+NUM_KERNELS = 11
 _LIB = None
 
 

@@ -144,6 +144,20 @@ class Plan:
         return {_native.lib().ptycho_kernel_name(k).decode(): (float(ms[k]), int(n[k]))
                 for k in range(_native.NUM_KERNELS)}
 
+    def regularise(self, O, mu_l1: float, mu_tv: float, eta: float, gO=None, loss_out=None, stream=None):
+        """ptycho_regularise: adds the object regulariser's gradient to ``gO`` (zeros if None)
+        and its value to ``loss_out`` (a float64 device scalar, zeros if None); returns both."""
+        Or = self._c64(O, self.numel_O, "O")
+        if gO is None:
+            gO = torch.zeros_like(O)
+        gr = self._c64(gO, self.numel_O, "gO")
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float64, device=O.device)
+        rc = _native.lib().ptycho_regularise(self._h_plan, _ptr(Or), float(mu_l1), float(mu_tv), float(eta),
+                                             _ptr(gr), _ptr(loss_out), _stream_handle(stream))
+        _check(rc, "ptycho_regularise")
+        return loss_out, gO
+
     def status(self) -> int:
         """Device status flags since the last query (synchronises; bit 0 = bad batch index,
         bit 1 = a column pass's bulk copy timed out)."""
@@ -326,8 +340,11 @@ class AdamState:
 
     def __init__(self, plan: Plan, lr_O: float, lr_P: float, beta1: float = 0.9, beta2: float = 0.999,
                  eps: float = 1e-8, device_counter: bool = False, lr_sigma: float = 0.0, lr_bg: float = 0.0,
-                 lr_delta: float = 0.0, with_z_gradient: bool = False):
+                 lr_delta: float = 0.0, with_z_gradient: bool = False, reg_l1: float = 0.0, reg_tv: float = 0.0,
+                 reg_eta: float = 1e-3):
         dev = plan.device
+        # optional object regularisation added by Plan.step (see Plan.regularise)
+        self.reg_l1, self.reg_tv, self.reg_eta = reg_l1, reg_tv, reg_eta
         # optional: sigma [J] and the background [F, F] are optimised too (updated in place by
         # Plan.step, which then needs them as float32 device tensors)
         self.lr_sigma, self.lr_bg = lr_sigma, lr_bg
@@ -357,6 +374,7 @@ class AdamState:
         s.mP, s.vP = self.mP.data_ptr(), self.vP.data_ptr()
         s.t_dev = None if self.t_dev is None else self.t_dev.data_ptr()
         s.lr_sigma, s.lr_bg, s.lr_delta = self.lr_sigma, self.lr_bg, self.lr_delta
+        s.reg_l1, s.reg_tv, s.reg_eta = self.reg_l1, self.reg_tv, self.reg_eta
         for name in ("m_sigma", "v_sigma", "m_bg", "v_bg", "m_delta", "v_delta", "g_z"):
             t = getattr(self, name)
             setattr(s, name, None if t is None else t.data_ptr())

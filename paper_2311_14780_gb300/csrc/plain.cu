@@ -14,7 +14,8 @@ extern "C" int ptycho_plain_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, f
                                  const float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
                                  double* loss_dev, void* stream) {
   if (!p || !s || !O || !P || !I_meas || !s->mO || !s->vO || !s->mP || !s->vP) return PTYCHO_EINVAL;
-  if (s->lr_sigma > 0.f || s->lr_bg > 0.f || s->lr_delta > 0.f || p->d_delta || s->g_z || p->czt)
+  if (s->lr_sigma > 0.f || s->lr_bg > 0.f || s->lr_delta > 0.f || p->d_delta || s->g_z || p->czt ||
+      s->reg_l1 != 0.f || s->reg_tv != 0.f)
     return PTYCHO_EUNSUPPORTED;                      // O and P at integer positions only
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->dev) return PTYCHO_EINVAL;

@@ -90,6 +90,8 @@ struct ptycho_plan {
   float2* d_shP = nullptr;                     // [nsets][B][L][F][F] shifted patches
   double* d_dpart = nullptr;                   // [J][L][F/W][2] position-gradient partials
   float* d_gdelta = nullptr;                   // [L][J][2] position gradient (ptycho_step)
+  double* d_reg_part = nullptr;                // [L][tiles] regulariser partials (allocated on first use)
+  long long reg_cap = 0;                       // capacity of d_reg_part
 
   // TMA tensor maps of each scratch set, viewed as [B*C*F rows][F columns] of 8-byte elements
   // with a W x min(F, 256) box (column passes); has_tma = 0 falls back to plain loads
@@ -131,7 +133,8 @@ struct CallArgs {
 };
 
 // Kernel kinds reported by ptycho_plan_profile_read (order matches PTYCHO_K_* in ptycho.h).
-enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kRemapAdj, kShift, kNumKinds };
+enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kRemapAdj, kShift, kReg,
+                  kNumKinds };
 
 // Records the start event of a profiled launch (no-op unless profiling); returns the pair index.
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);
@@ -143,6 +146,11 @@ void prof_end(ptycho_plan& p, long long idx, cudaStream_t st);
 // the HBM budget).
 int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** out);
 constexpr long long kServeBatchEvals = 128;
+
+// Object regulariser (reg.cu): adds R to *loss (if not null) and dR to gO on stream st.
+bool reg_args_ok(float mu_l1, float mu_tv, float eta);
+int regularise(ptycho_plan& p, const float2* O, float mu_l1, float mu_tv, float eta, float2* gO, double* loss,
+               cudaStream_t st);
 
 // Defined once per frame size in kern_<F>.cu.
 template <int F> int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st);

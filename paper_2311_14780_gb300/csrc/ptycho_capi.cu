@@ -289,7 +289,7 @@ void free_plan(ptycho_plan* p) {
                   p->d_rt_w, p->d_S, p->d_Ipart, p->d_D, p->d_Gt, p->d_loss_part, p->d_gO, p->d_gP, p->d_status,
                   p->d_sig_part, p->d_gbg_set, p->d_gsig, p->d_gbg, p->d_gPs, p->d_shT, p->d_shQ, p->d_shP,
                   p->d_dpart, p->d_gdelta, p->d_tap_dz, p->d_z_part, p->d_czt_chirp, p->d_czt_hf,
-                  p->d_czt_ha, p->d_czt_tw2};
+                  p->d_czt_ha, p->d_czt_tw2, p->d_reg_part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -734,7 +734,7 @@ int ptycho_plan_profile_read(ptycho_plan_t* p, double* ms, int64_t* launches) {
 
 const char* ptycho_kernel_name(int kind) {
   static const char* names[] = {"row_fwd", "col_fwd", "loss", "col_adj", "row_adj", "obj_grad", "loss_reduce", "adam",
-                                "remap_adj", "shift"};
+                                "remap_adj", "shift", "regulariser"};
   return (kind >= 0 && kind < ptycho::kNumKinds) ? names[kind] : "unknown";
 }
 
@@ -886,12 +886,20 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
   if (opt_sigma && (!sigma || !s->m_sigma || !s->v_sigma)) return PTYCHO_EINVAL;
   if (opt_bg && (!bg || !s->m_bg || !s->v_bg)) return PTYCHO_EINVAL;
   if (opt_delta && (!p->d_delta || !s->m_delta || !s->v_delta)) return PTYCHO_EINVAL;
+  const bool reg = s->reg_l1 != 0.f || s->reg_tv != 0.f;
+  if (reg && !ptycho::reg_args_ok(s->reg_l1, s->reg_tv, s->reg_eta)) return PTYCHO_EINVAL;
   int rc = ptycho_adjoint_ex(p, O, P, sigma, bg, I_meas, mask, mask_per_frame, batch_idx, nbatch,
                              reinterpret_cast<float*>(p->d_gO), reinterpret_cast<float*>(p->d_gP),
                              opt_sigma ? p->d_gsig : nullptr, opt_bg ? p->d_gbg : nullptr,
                              opt_delta ? p->d_gdelta : nullptr, s->g_z, loss_dev, stream);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  if (reg) {
+    // the regulariser's value joins the loss and its gradient the object gradient
+    rc = ptycho::regularise(*p, reinterpret_cast<const float2*>(O), s->reg_l1, s->reg_tv, s->reg_eta, p->d_gO,
+                            loss_dev, st);
+    if (rc) return rc;
+  }
   const long long nO = 2 * p->O_numel, nP = 2 * p->P_numel;
   const long long FF = (long long)p->F * p->F;
   const long long nD = 2ll * p->L * p->J;

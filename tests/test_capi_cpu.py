@@ -134,6 +134,19 @@ def test_tilt_correct_rejects_bad_arguments_on_the_host(lib):
     assert ap(64, 0, None, None, -math.inf, math.inf, None, None, None) == 0
 
 
+def test_regularise_rejects_bad_arguments_on_the_host(lib):
+    f = lib.ptycho_regularise
+    a = ctypes.c_void_p(0x1000)
+    assert f(None, a, 0.1, 0.1, 1e-3, a, None, None) == -1
+    fake_plan = ctypes.c_void_p(0x2000)        # never dereferenced: the checks below come first
+    assert f(fake_plan, None, 0.1, 0.1, 1e-3, a, None, None) == -1
+    assert f(fake_plan, a, 0.1, 0.1, 1e-3, None, None, None) == -1
+    assert f(fake_plan, a, -0.1, 0.1, 1e-3, a, None, None) == -1
+    assert f(fake_plan, a, 0.1, 0.1, 0.0, a, None, None) == -1
+    assert f(fake_plan, a, math.nan, 0.1, 1e-3, a, None, None) == -1
+    assert f(fake_plan, a, 0.1, math.inf, 1e-3, a, None, None) == -1
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2311_14780_gb300 import _native
     monkeypatch.setattr(_native, "_LIB", None)
