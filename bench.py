@@ -396,11 +396,11 @@ def run_ours(args, rank: int, world: int):
         bgt = torch.ones(w.F, w.F, dtype=torch.float32, device=dev)
         O2, P2 = O.clone(), P.clone()
         base_ms = timed(lambda: plan.step(st, O2, P2, Im, loss_out=loss), args.corrections_steps)
+        st_reg = AdamState(plan, lr_O=1e-3, lr_P=1e-3, reg_l1=1e-2, reg_tv=1e-1, reg_eta=1e-3)
+        reg_ms = timed(lambda: plan.step(st_reg, O2, P2, Im, loss_out=loss), args.corrections_steps)
         plan.set_offsets(delta)
         st_pos = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2)
         pos_ms = timed(lambda: plan.step(st_pos, O2, P2, Im, loss_out=loss), args.corrections_steps)
-        st_reg = AdamState(plan, lr_O=1e-3, lr_P=1e-3, reg_l1=1e-2, reg_tv=1e-1, reg_eta=1e-3)
-        reg_ms = timed(lambda: plan.step(st_reg, O2, P2, Im, loss_out=loss), args.corrections_steps)
         st_all = AdamState(plan, lr_O=1e-3, lr_P=1e-3, lr_delta=1e-2, lr_sigma=1e-2, lr_bg=1e-2)
         all_ms = timed(lambda: plan.step(st_all, O2, P2, Im, sig, bgt, loss_out=loss), args.corrections_steps)
         z_ms = None
