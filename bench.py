@@ -232,6 +232,21 @@ def ncu_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, t_ms_max: float) -> float:
+    """Units all ranks processed (each rank runs the same workload) per second of the slowest rank."""
+    return units_per_step * steps * world / (t_ms_max / 1e3)
+
+
 def algorithmic_flops_per_eval(F: int) -> float:
     """Two orthonormal 2D DFTs (forward + adjoint) at 5 N log2 N flops each, N = F^2."""
     return 2 * 5.0 * F * F * math.log2(F * F)
@@ -309,13 +324,9 @@ def run_ours(args, rank: int, world: int):
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_ms = float(sum(step_ms))
-    if dist:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     clk = clocks.stop()
-    value = evals * args.steps * world / (t_ms / 1e3)
+    value = whole_job_rate(evals, args.steps, world, t_ms)
 
     # ---- per-kernel event timing for the roofline (same workload, same stream) --------
     plan.profile(True)
@@ -364,12 +375,8 @@ def run_ours(args, rank: int, world: int):
             loss_host.copy_(loss, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1)
-        if dist:
-            tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": evals * e_steps * world / (e_ms / 1e3), "unit": UNIT,
+        e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        e2e = {"value": whole_job_rate(evals, e_steps, world, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(Ih_pinned.numel() * 4), "d2h_bytes_per_step": 8,
                "note": "pinned host I_meas copied to the GPU every step; loss read back every step"}
 
