@@ -353,7 +353,18 @@ def run_ours(args, rank: int, world: int):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no FP32 figure in "
                                "MEASURED_PEAKS.json)",
                 "units_per_launch": units_per_launch, "flops_per_unit": 0.25 * flops_eval,
-                "avg_launch_ms": kern_ms / kern_n}
+                "avg_launch_ms": kern_ms / kern_n,
+                "note": "launch durations are CUDA events on the launch stream with three position batches in "
+                        "flight, so each launch shares the GPU with the other streams' kernels"}
+        tr = roof["traffic"]
+        if tr:
+            # the scratch round trips make the pass memory-heavy: its actual DRAM rate against HBM
+            try:
+                hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+            except Exception:
+                hbm = 6800.0
+            roof["traffic_gbs"] = tr / (kern_ms / kern_n / 1e3) / 1e9
+            roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / hbm
     step_total = sum(v[0] for v in prof.values()) / prof_steps
     step_flops = flops_eval * evals
     kernels = {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps,
