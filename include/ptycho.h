@@ -65,9 +65,10 @@ extern "C" {
  *   copies save.  NO_TMA wins when both are given.
  * UNFUSED_ROW_ADJ: one block of the adjoint row pass per probe mode, each mode's object-
  *   gradient row left in the scratch for the object-gradient kernel (always the case for
- *   F = 512).  The default for F <= 256, whenever all modes of a position fit the scratch and
- *   T*M <= 256 (T = 4, 8, 16 threads per row for F = 64, 128, 256), takes all modes of a
- *   wavelength per block: the probe rows
+ *   F = 512 with fewer than 8 modes).  The default for F <= 256, and for F = 512 from 8 modes
+ *   up, whenever all modes of a position fit the scratch and T*M <= 256 (T = 4, 8, 16, 16
+ *   threads per row for F = 64, 128, 256, 512), takes all modes of a wavelength per block:
+ *   the probe rows
  *   stay in shared memory for the batch and the object-gradient rows are summed over the
  *   modes before they are written.
  * STAGED_COLUMNS: whenever all modes of a position fit the scratch, run each column block over

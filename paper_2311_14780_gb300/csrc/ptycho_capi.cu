@@ -558,7 +558,9 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
       default: T = ptycho::FftShape<512>::N1; break;
     }
     // measured: at F = 512 the fused kernel's registers (two 32-value rows per thread) cost
-    // more occupancy than the probe reuse saves, so F = 512 keeps one block per mode
+    // more occupancy than the probe reuse saves with few modes (4 modes x 3 wavelengths: 8 %
+    // slower), but from 8 modes up the object-gradient kernel's M-fold smaller read wins (8 x 3:
+    // 2 % faster; 10 modes x 6 wavelengths, 512^2: 7 %), so F = 512 fuses from M = 8
     if (p->store && T * g->M <= 256) {
       int rpb = 1;
       while (2 * rpb * T * g->M <= 128 && 2 * rpb <= F) rpb *= 2;
@@ -570,7 +572,7 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
       }
       if (smem <= ptycho::kRowAdjLSmemMax) {
         p->adj_l_ok = 1;
-        p->adj_l = !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) && F <= 256;
+        p->adj_l = !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) && (F <= 256 || g->M >= 8);
         p->rpb_adj = rpb;
         // enough blocks for three per SM: split the batch's positions, each split summing its
         // probe gradient into a buffer of its own (bounded to 512 MB in all)

@@ -117,6 +117,20 @@ def strong_z(F):
     return F * 15e-6 / 0.5
 
 
+@pytest.mark.parametrize("flags", [0, 32])
+def test_fused_row_adjoint_at_512_with_eight_modes(dev, flags):
+    """F = 512 with 8 modes takes the fused row adjoint (all modes of a wavelength per block,
+    object-gradient rows summed over the modes in shared memory); flag 32 forces the per-mode
+    kernel.  Several position batches and splits."""
+    w = syn.tiny_workload(F=512, L=1, M=8, n_side=3, step=64, seed=77, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=12)
+    plan = case.plan(flags=flags, scratch_bytes=3 * 8 * 512 * 512 * 8)
+    assert_ok(check_all(case, plan))
+    assert_ok(check_all(case, plan, frames=[7, 0, 4]))
+    plan.close()
+
+
 @pytest.mark.parametrize("F", [64, 128, 256, 512])
 @pytest.mark.parametrize("loss", ["amplitude", "poisson"])
 def test_tiny_all_frame_sizes(dev, F, loss):
