@@ -7,11 +7,12 @@
 // and, with g = dR/dRe + i dR/dIm = (dR/da) O / a,
 //   dR/da[r][c] = mu_l1 + mu_tv (-(dx + dy)/t [r][c] + dx/t [r][c-1] + dy/t [r-1][c]).
 //
-// One block owns a kRegTX x kRegTY tile of one object.  It stages the amplitudes of the tile and
-// a one-pixel halo in shared memory, forms dx/t and dy/t for the tile and its upper and left
-// halo, then every thread adds its pixel's gradient into gO (each pixel has one owner: no
-// atomics) and the block's share of R goes to a per-tile FP64 partial; a second kernel adds the
-// partials to the loss in a fixed order.  HBM-bound: O read, gO read and written, 24 B per pixel.
+// One block owns a kRegTX x kRegTY tile of one object, kRegRows rows per thread.  It stages the
+// amplitudes of the tile and a one-pixel halo in shared memory, forms dx/t and dy/t for the tile
+// and its upper and left halo, then every thread adds its pixels' gradients into gO (each pixel
+// has one owner: no atomics) and the block's share of R goes to a per-tile FP64 partial; a second
+// kernel adds the partials to the loss in a fixed order.  HBM-bound: O read, gO read and
+// written, 24 B per pixel.
 #include <math.h>
 
 #include "plan.h"
@@ -19,8 +20,9 @@
 namespace ptycho {
 namespace {
 
-constexpr int kRegTX = 32, kRegTY = 8;           // tile: columns x rows (one thread per pixel)
-constexpr int kRegThreads = kRegTX * kRegTY;
+constexpr int kRegTX = 32, kRegTY = 32;          // tile: columns x rows
+constexpr int kRegRows = 4;                      // rows per thread (threads: kRegTX x kRegTY / kRegRows)
+constexpr int kRegThreads = kRegTX * kRegTY / kRegRows;
 
 struct RegArgs {
   const float2* O;
@@ -76,22 +78,27 @@ __global__ void __launch_bounds__(kRegThreads) k_reg(RegArgs r) {
     qy[i][j] = py;
   }
   __syncthreads();
-  const int ty = threadIdx.x / kRegTX, tc = threadIdx.x % kRegTX;
-  const int rr = r0 + ty, cc = c0 + tc;
+  const int tc = threadIdx.x % kRegTX, ty0 = threadIdx.x / kRegTX;
+  const int cc = c0 + tc;
   double term = 0.0;
-  if (rr < H && cc < W) {
-    const int i = ty + 1, j = tc + 1;
-    const float a = as[i][j];
-    const float dx = cc + 1 < W ? as[i][j + 1] - a : 0.f;
-    const float dy = rr + 1 < H ? as[i + 1][j] - a : 0.f;
-    const float t = sqrtf(fmaf(dx, dx, fmaf(dy, dy, e2)));
-    const float dRda = r.mu1 + r.mutv * ((qx[i][j - 1] + qy[i - 1][j]) - (qx[i][j] + qy[i][j]));
-    const long long idx = r.off[l] + (long long)rr * W + cc;
-    const float2 o = Ol[(long long)rr * W + cc];
-    const float s = dRda / a;
-    const float2 g = r.gO[idx];
-    r.gO[idx] = make_float2(fmaf(s, o.x, g.x), fmaf(s, o.y, g.y));
-    term = (double)(r.mu1 * a) + (double)(r.mutv * t);
+#pragma unroll
+  for (int k = 0; k < kRegRows; ++k) {
+    const int ty = ty0 + k * (kRegThreads / kRegTX);
+    const int rr = r0 + ty;
+    if (rr < H && cc < W) {
+      const int i = ty + 1, j = tc + 1;
+      const float a = as[i][j];
+      const float dx = cc + 1 < W ? as[i][j + 1] - a : 0.f;
+      const float dy = rr + 1 < H ? as[i + 1][j] - a : 0.f;
+      const float t = sqrtf(fmaf(dx, dx, fmaf(dy, dy, e2)));
+      const float dRda = r.mu1 + r.mutv * ((qx[i][j - 1] + qy[i - 1][j]) - (qx[i][j] + qy[i][j]));
+      const long long idx = r.off[l] + (long long)rr * W + cc;
+      const float2 o = Ol[(long long)rr * W + cc];
+      const float s = dRda / a;
+      const float2 g = r.gO[idx];
+      r.gO[idx] = make_float2(fmaf(s, o.x, g.x), fmaf(s, o.y, g.y));
+      term += (double)(r.mu1 * a) + (double)(r.mutv * t);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
