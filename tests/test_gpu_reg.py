@@ -29,7 +29,7 @@ def c64(x):
 
 @pytest.mark.parametrize("H,mu1,mutv,eta", [(81, 0.3, 0.7, 0.05), (96, 0.0, 1.0, 1e-3), (125, 0.5, 0.0, 0.01)])
 def test_regularise_matches_the_oracle(dev, H, mu1, mutv, eta):
-    """Objects of H x (H + 2) pixels per wavelength (tiles of 32 x 8 with ragged edges), L = 3;
+    """Objects of H x (H + 2) pixels per wavelength (tiles of 32 x 32 with ragged edges), L = 3;
     gradient and value added onto non-zero buffers."""
     from paper_2311_14780_gb300 import pack_objects, plan_for
     w = syn.tiny_workload(F=64, L=3, M=1, n_side=2, step=8, seed=H, H=H)
