@@ -425,8 +425,18 @@ __device__ __forceinline__ void predict_pixel(const LossArgs& la, const float* I
   if (la.remap) {
     valid = tb >= 0;
     if (!valid) return;
-    float i00 = model_I(Ip, nullptr, G, FF, tb), i01 = model_I(Ip, nullptr, G, FF, tb + 1);
-    float i10 = model_I(Ip, nullptr, G, FF, tb + F), i11 = model_I(Ip, nullptr, G, FF, tb + F + 1);
+    float i00, i01, i10, i11;
+    if (G == 1) {                                     // one intensity slice (uniform branch)
+      i00 = Ip[tb];
+      i01 = Ip[tb + 1];
+      i10 = Ip[tb + F];
+      i11 = Ip[tb + F + 1];
+    } else {
+      i00 = model_I(Ip, nullptr, G, FF, tb);
+      i01 = model_I(Ip, nullptr, G, FF, tb + 1);
+      i10 = model_I(Ip, nullptr, G, FF, tb + F);
+      i11 = model_I(Ip, nullptr, G, FF, tb + F + 1);
+    }
     Is = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
     if (la.bg) {
       const float b00 = __ldg(la.bg + tb), b01 = __ldg(la.bg + tb + 1);
@@ -437,7 +447,7 @@ __device__ __forceinline__ void predict_pixel(const LossArgs& la, const float* I
     srow = ((1.f - w.y) * i10 + w.y * i11) - ((1.f - w.y) * i00 + w.y * i01);
     scol = (1.f - w.x) * (i01 - i00) + w.x * (i11 - i10);
   } else {
-    Is = model_I(Ip, nullptr, G, FF, q);
+    Is = G == 1 ? Ip[q] : model_I(Ip, nullptr, G, FF, q);
     if (la.bg) Ib = __ldg(la.bg + q);
   }
 }
