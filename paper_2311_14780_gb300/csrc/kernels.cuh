@@ -385,11 +385,21 @@ struct LossArgs {
   double* z_part;                // [nbatch][loss_blocks] sums of D * d(R I)/dz, or null
 };
 
-__device__ __forceinline__ float model_I(const float* Ip, const float* bg, int G, int FF, int u) {
-  float s = 0.f;
-  for (int g = 0; g < G; ++g) s += Ip[(long long)g * FF + u];
-  if (bg) s += __ldg(bg + u);
-  return s;
+// Model intensity at pixel u: the G intensity slices added in slice order (small G unrolled; the
+// rounding is that of the loop, which starts from 0 + slice 0).
+__device__ __forceinline__ float model_I(const float* Ip, int G, int FF, int u) {
+  const float* p = Ip + u;
+  switch (G) {
+    case 1: return p[0];
+    case 2: return p[0] + p[FF];
+    case 3: return (p[0] + p[FF]) + p[2 * FF];
+    case 4: return ((p[0] + p[FF]) + p[2 * FF]) + p[3 * FF];
+    default: {
+      float s = 0.f;
+      for (int g = 0; g < G; ++g, p += FF) s += *p;
+      return s;
+    }
+  }
 }
 
 // Poisson deviance per pixel, I_hat * (r - 1 - log r) with r = Ie / I_hat, without the
@@ -432,10 +442,10 @@ __device__ __forceinline__ void predict_pixel(const LossArgs& la, const float* I
       i10 = Ip[tb + F];
       i11 = Ip[tb + F + 1];
     } else {
-      i00 = model_I(Ip, nullptr, G, FF, tb);
-      i01 = model_I(Ip, nullptr, G, FF, tb + 1);
-      i10 = model_I(Ip, nullptr, G, FF, tb + F);
-      i11 = model_I(Ip, nullptr, G, FF, tb + F + 1);
+      i00 = model_I(Ip, G, FF, tb);
+      i01 = model_I(Ip, G, FF, tb + 1);
+      i10 = model_I(Ip, G, FF, tb + F);
+      i11 = model_I(Ip, G, FF, tb + F + 1);
     }
     Is = (1.f - w.x) * ((1.f - w.y) * i00 + w.y * i01) + w.x * ((1.f - w.y) * i10 + w.y * i11);
     if (la.bg) {
@@ -447,7 +457,7 @@ __device__ __forceinline__ void predict_pixel(const LossArgs& la, const float* I
     srow = ((1.f - w.y) * i10 + w.y * i11) - ((1.f - w.y) * i00 + w.y * i01);
     scol = (1.f - w.x) * (i01 - i00) + w.x * (i11 - i10);
   } else {
-    Is = G == 1 ? Ip[q] : model_I(Ip, nullptr, G, FF, q);
+    Is = model_I(Ip, G, FF, q);
     if (la.bg) Ib = __ldg(la.bg + q);
   }
 }
