@@ -673,12 +673,11 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
   for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
     const int k = e / W, ce = e % W;
     const int u = ((k + F / 2) & (F - 1)) * F + ((col0 + ce + F / 2) & (F - 1));
-    gt[k * W + ce] = Gb[u] * scale;
+    gt[k * W + ce] = Gb[u] * (STORE ? scale : scale / (float)F);   // recomputed Psi: the 1/F folded in
   }
   __syncthreads();
   const int col = col0 + c;
   const int m0 = g * a.MG, m1 = min(a.chunk_len, m0 + a.MG);
-  const float inv = 1.0f / (float)F;
   for (int cm = m0; cm < m1; ++cm) {
     float2* base = S + ((long long)b * a.C + cm) * F * F + col;
     float2 v[N2];
@@ -689,8 +688,6 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) v[n2] = base[(long long)(t + N1 * n2) * F];
       fft_fwd_I2O<F>(v, t, smem + c * Xch<F>::region_cols, a.tw, BlockSync{});
-#pragma unroll
-      for (int sl = 0; sl < N2; ++sl) v[sl] = cscale(v[sl], inv);
     }
 #pragma unroll
     for (int sl = 0; sl < N2; ++sl) v[sl] = cscale(v[sl], gt[idxO<F>(t, sl) * W + c]);
