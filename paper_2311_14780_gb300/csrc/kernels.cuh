@@ -1062,12 +1062,20 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
       reg[c] = cscale(cconjmul(Psm[vec * F + c], v[n2]), s);            // conj(sigma P) chi
     }
     __syncthreads();
+    float2* dst = S + (((long long)b * a.C + slot0) * F + row0) * F;      // the block's rpb rows, contiguous
     for (int e = threadIdx.x; e < rpb * F; e += blockDim.x) {           // modes added in order
       const int rr2 = e / F, c = e % F;
       const float2* red = Sst + (buf * V + rr2 * M) * RR + c;
       float2 sum = red[0];
-      for (int mm = 1; mm < M; ++mm) sum = cadd(sum, red[mm * RR]);
-      S[(((long long)b * a.C + slot0) * F + row0 + rr2) * F + c] = sum;
+      switch (M) {                                    // small mode counts unrolled, same order
+        case 1: break;
+        case 2: sum = cadd(sum, red[RR]); break;
+        case 3: sum = cadd(cadd(sum, red[RR]), red[2 * RR]); break;
+        case 4: sum = cadd(cadd(cadd(sum, red[RR]), red[2 * RR]), red[3 * RR]); break;
+        default:
+          for (int mm = 1; mm < M; ++mm) sum = cadd(sum, red[mm * RR]);
+      }
+      dst[e] = sum;
     }
     b = bn;
   }
