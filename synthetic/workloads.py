@@ -19,7 +19,7 @@ from typing import List, Optional, Tuple
 
 import numpy as np
 
-try:  # scipy is present on both the build container and the GPU machine
+try:  # scipy is normally present; the FFT fallback below covers its absence
     from scipy.ndimage import gaussian_filter as _gaussian_filter
 except Exception:  # pragma: no cover
     _gaussian_filter = None
