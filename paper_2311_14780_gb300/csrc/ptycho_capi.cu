@@ -536,7 +536,7 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
     case 256: colblocks = F / ptycho::ColCfg<256>::W; break;
     default: colblocks = F / ptycho::ColCfg<512>::W; break;
   }
-  const long long target = 4ll * p->sms;
+  const long long target = 2ll * p->sms;   // column blocks wanted: mode groups only below two per SM
   long long G = (target + (long long)colblocks * p->B - 1) / ((long long)colblocks * p->B);
   if (g->col_groups > 0) G = g->col_groups;
   G = std::max<long long>(1, std::min<long long>(G, p->C));
