@@ -66,3 +66,19 @@ def test_header_fields_are_all_bound(tmp_path):
         last, ftype = cls._fields_[-1]
         end = getattr(cls, last).offset + ctypes.sizeof(ftype)
         assert end <= table[(cname, "size")] < end + 8, cname
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Each bound entry point takes as many arguments as its prototype in ptycho.h."""
+    import re
+    from paper_2311_14780_gb300 import _native
+    text = open(os.path.join(ROOT, "include", "ptycho.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(ptycho_[A-Za-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+        name, args = m.group(1), m.group(2).strip()
+        protos[name] = 0 if args in ("", "void") else len(args.split(","))
+    for name, _, argtypes in _native.SIGNATURES:
+        assert name in protos, name
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+    assert set(protos) == {n for n, _, _ in _native.SIGNATURES}      # every prototype is bound
