@@ -66,18 +66,15 @@ extern "C" int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J
   if (L > ptycho::kMaxL || fft_shape(F, &N1, &N2) != PTYCHO_OK) return PTYCHO_EUNSUPPORTED;
   for (int l = 0; l < L; ++l)
     if (obj_h[l] < F || obj_w[l] < F) return PTYCHO_EINVAL;
-  for (int l = 0; l < L; ++l)
-    for (int j = 0; j < J; ++j) {
-      const int y = pos[(l * J + j) * 2], x = pos[(l * J + j) * 2 + 1];
-      if (y < 0 || x < 0 || y > obj_h[l] - F || x > obj_w[l] - F) return PTYCHO_ERANGE;
-    }
 
   // layout of the fixed array: twiddles | positions | position list | status | intensity
-  // sums [B][F][F] | field scratch [B][C][F][F]
+  // sums [B][F][F] | field scratch [B][C][F][F]; decided (and a problem that cannot fit
+  // refused) before any position is read
   const long long FF = (long long)F * F;
+  const long long LJ = (long long)L * J;
   const long long off_tw = 0;
   const long long off_pos = align256(off_tw + (long long)F * (long long)sizeof(float2));
-  const long long off_ident = align256(off_pos + (long long)L * J * 2 * (long long)sizeof(int32_t));
+  const long long off_ident = align256(off_pos + LJ * 2 * (long long)sizeof(int32_t));
   const long long off_status = align256(off_ident + (long long)J * (long long)sizeof(int32_t));
   const long long off_data = align256(off_status + (long long)sizeof(int));
   const long long avail = (long long)PTYCHO_NOALLOC_SCRATCH_BYTES - off_data;
@@ -93,6 +90,14 @@ extern "C" int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J
     nchunks = (int)((LM + C - 1) / C);
   } else {
     return PTYCHO_ETOOLARGE;
+  }
+  if (off_data + align256((long long)B * frame_f) + (long long)B * C * frame_c > (long long)PTYCHO_NOALLOC_SCRATCH_BYTES)
+    return PTYCHO_ETOOLARGE;
+
+  for (long long e = 0; e < LJ; ++e) {
+    const long long l = e / J;
+    const int y = pos[2 * e], x = pos[2 * e + 1];
+    if (y < 0 || x < 0 || y > obj_h[l] - F || x > obj_w[l] - F) return PTYCHO_ERANGE;
   }
 
   int dev = -1;
@@ -110,7 +115,7 @@ extern "C" int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J
       tw[k2 * N1 + t] = make_float2((float)cos(ang), (float)sin(ang));
     }
   if (cudaMemcpyAsync(base + off_tw, tw, sizeof(float2) * (size_t)F, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(base + off_pos, pos, sizeof(int32_t) * (size_t)L * J * 2, cudaMemcpyHostToDevice, st) !=
+      cudaMemcpyAsync(base + off_pos, pos, sizeof(int32_t) * (size_t)LJ * 2, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemsetAsync(base + off_status, 0, sizeof(int), st) != cudaSuccess)
     return PTYCHO_ECUDA;
@@ -147,8 +152,6 @@ extern "C" int ptycho_forward_noalloc(int32_t L, int32_t M, int32_t F, int32_t J
   view.d_status = reinterpret_cast<int*>(base + off_status);
   view.d_Ipart = reinterpret_cast<float*>(base + off_data);
   view.d_S = reinterpret_cast<float2*>(base + off_data + align256((long long)B * frame_f));
-  if (off_data + align256((long long)B * frame_f) + (long long)B * C * frame_c > (long long)PTYCHO_NOALLOC_SCRATCH_BYTES)
-    return PTYCHO_ETOOLARGE;
 
   ptycho::CallArgs c{};
   c.kind = ptycho::CallKind::Forward;

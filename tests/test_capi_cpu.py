@@ -153,3 +153,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_native, "lib_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _native.lib()
+
+
+def test_noalloc_forward_rejects_what_it_cannot_do_before_touching_the_gpu(lib):
+    """The allocation-free forward entry point checks every size and position on the host
+    before it asks for a device: an unsupported frame size, a problem whose tables alone do
+    not fit its fixed array, and a patch outside its object.  The data pointers here are
+    placeholders that are never dereferenced."""
+    ip = ctypes.POINTER(ctypes.c_int32)
+    fake = ctypes.c_void_p(256)
+
+    def call(L, M, F, J, H, pos):
+        h = np.full(L, H, np.int32)
+        w = np.full(L, H, np.int32)
+        pos = np.ascontiguousarray(pos, np.int32)
+        return lib.ptycho_forward_noalloc(L, M, F, J, h.ctypes.data_as(ip), w.ctypes.data_as(ip),
+                                          pos.ctypes.data_as(ip), fake, fake, None, None, fake, None)
+
+    assert call(1, 1, 100, 4, 128, np.zeros((1, 4, 2))) == -6                 # F not in {64,128,256,512}
+    assert call(1, 1, 64, 3_000_000, 128, np.zeros((1, 3_000_000, 2))) == -7  # position tables exceed the array
+    assert b"fixed array" in lib.ptycho_strerror(-7)
+    bad = np.zeros((2, 4, 2))
+    bad[1, 3] = (70, 0)                                                       # 70 + 64 > 128
+    assert call(2, 1, 64, 4, 128, bad) == -2
+    assert call(1, 1, 64, 0, 128, np.zeros((1, 1, 2))) == -1                  # no positions

@@ -1,8 +1,15 @@
 """GPU path vs the FP64 oracle on the same seeded inputs.
 
 Bars (from the stated accuracy targets): relative L2 <= 1e-5 on predicted intensities
-and on the loss, <= 1e-4 on the gradients.  Inputs are complex64 on the GPU and the
-same values in FP64 for the oracle.
+and on the loss, <= 1e-4 on the gradients.  Beside every L2 bar sits an element-wise
+bar with the same number in the max norm: no pixel of a predicted frame may differ from
+the oracle by more than 1e-5 of that frame's largest value, and no element of a gradient
+array by more than 1e-4 of the array's largest magnitude.  Evaluating the oracle's own
+steps in complex64 (numpy keeps complex64 FFTs in single precision) departs from FP64 by
+at most 2.1e-7 (intensities, per frame) and 5.3e-6 (gradients) in that norm on configs
+1, 2 and the 128^2 x 8 modes x 5 wavelengths sweep point, so both element-wise bars sit
+20-50x above the precision floor.  Inputs are complex64 on the GPU and the same values
+in FP64 for the oracle.
 """
 import math
 
@@ -18,12 +25,28 @@ pytestmark = pytest.mark.gpu
 TOL_I = 1e-5
 TOL_L = 1e-5
 TOL_G = 1e-4
+TOL_I_MAX = 1e-5      # per frame: max |GPU - oracle| / max |oracle frame|
+TOL_G_MAX = 1e-4      # per array: max |GPU - oracle| / max |oracle|
 
 
 def rel(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def max_rel(a, b):
+    """Largest element-wise deviation relative to the largest reference magnitude."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def max_rel_frames(a, b):
+    """max_rel taken frame by frame ([J, F, F] stacks); the worst frame."""
+    a = np.asarray(a).reshape(len(a), -1)
+    b = np.asarray(b).reshape(len(b), -1)
+    return float((np.abs(a - b).max(1) / np.maximum(np.abs(b).max(1), 1e-300)).max())
 
 
 @pytest.fixture(scope="module")
@@ -100,8 +123,10 @@ def check_all(case, plan, frames=None):
     La, gO, gP = plan.adjoint(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t, batch)
     Lr, gOr, gPr = case.oracle_grad(frames)
     gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    gO, gP = gO.cpu().numpy(), gP.cpu().numpy()
     out = dict(I=e_I, L=abs(Lg - Lr) / abs(Lr), La=abs(float(La.item()) - Lr) / abs(Lr),
-               gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr), status=plan.status())
+               gO=rel(gO, gOr), gP=rel(gP, gPr), I_max=max_rel_frames(Ip, Ir), gO_max=max_rel(gO, gOr),
+               gP_max=max_rel(gP, gPr), status=plan.status())
     return out
 
 
@@ -110,6 +135,8 @@ def assert_ok(err):
     assert err["I"] < TOL_I, err
     assert err["L"] < TOL_L and err["La"] < TOL_L, err
     assert err["gO"] < TOL_G and err["gP"] < TOL_G, err
+    assert err["I_max"] < TOL_I_MAX, err
+    assert err["gO_max"] < TOL_G_MAX and err["gP_max"] < TOL_G_MAX, err
 
 
 # z chosen so that the remap visibly distorts small frames (F p / z ~ 0.5)
@@ -217,8 +244,10 @@ def _config2_sampled(dev, O_eval, P_eval, sample, seed=7):
     La, gO, gP = plan.adjoint(O, P, Im, batch=bt)
     Lr, gOr, gPr = orc.gradient(O0, P0, w.pos, Ih, "poisson", eps, None, None, None, taps, frames=sample)
     gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    gO, gP = gO.cpu().numpy(), gP.cpu().numpy()
     err = dict(I=rel(Ip[sample], Ir), L=abs(float(La.item()) - Lr) / abs(Lr), La=0.0,
-               gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr))
+               gO=rel(gO, gOr), gP=rel(gP, gPr), I_max=max_rel_frames(Ip[sample], Ir), gO_max=max_rel(gO, gOr),
+               gP_max=max_rel(gP, gPr))
     plan.close()
     return err, (w, O0, P0, Ih, eps, taps, gOr, gPr)
 
@@ -243,13 +272,17 @@ def test_config2_full_size_flat_object_start(dev):
     w = syn.config2()
     sample = sorted(np.random.default_rng(0).choice(w.J, size=6, replace=False).tolist())
     err, (w, O0, P0, Ih, eps, taps, gOr, gPr) = _config2_sampled(dev, w.O0, w.P0, sample)
-    assert err["I"] < TOL_I and err["L"] < TOL_L, err
+    assert err["I"] < TOL_I and err["L"] < TOL_L and err["I_max"] < TOL_I_MAX, err
     _, gO32, gP32 = orc.gradient([o.astype(np.complex64) for o in O0], P0.astype(np.complex64), w.pos, Ih,
                                  "poisson", eps, None, None, None, taps, frames=sample)
-    floor_O = rel(np.concatenate([g.reshape(-1) for g in gO32]), gOr)
-    floor_P = rel(gP32, gPr)
+    gO32 = np.concatenate([g.reshape(-1) for g in gO32])
+    floor_O, floor_P = rel(gO32, gOr), rel(gP32, gPr)
     assert err["gO"] < max(TOL_G, 1.5 * floor_O), (err, floor_O)
     assert err["gP"] < max(TOL_G, 1.5 * floor_P), (err, floor_P)
+    # element-wise: the same reading, with the complex64 floor taken in the max norm
+    mfloor_O, mfloor_P = max_rel(gO32, gOr), max_rel(gP32, gPr)
+    assert err["gO_max"] < max(TOL_G_MAX, 1.5 * mfloor_O), (err, mfloor_O)
+    assert err["gP_max"] < max(TOL_G_MAX, 1.5 * mfloor_P), (err, mfloor_P)
 
 
 def test_autograd_function_directional_derivative(dev):
@@ -330,8 +363,10 @@ def _sampled_full_size(dev, w, n_frames, n_grad, seed):
     La, gO, gP = plan.adjoint(O, P, torch.as_tensor(Ih, device=dev).contiguous(), batch=bt)
     Lr, gOr, gPr = orc.gradient(O0, P0, w.pos, Ih, w.loss, eps, None, None, None, taps, frames=gframes)
     gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    gO, gP = gO.cpu().numpy(), gP.cpu().numpy()
     err = dict(I=rel(Ip[frames], Ir), L=abs(float(La.item()) - Lr) / abs(Lr), La=0.0,
-               gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr))
+               gO=rel(gO, gOr), gP=rel(gP, gPr), I_max=max_rel_frames(Ip[frames], Ir), gO_max=max_rel(gO, gOr),
+               gP_max=max_rel(gP, gPr))
     plan.close()
     return err
 
@@ -351,6 +386,57 @@ def test_config4_full_size_sampled(dev):
     positions): sampled frames and the gradient of one position against the oracle."""
     w = syn.config4()
     assert_ok(_sampled_full_size(dev, w, n_frames=2, n_grad=1, seed=4))
+
+
+def _full_size_all_positions(dev, w, seed):
+    """Every position of a full-size workload under the plan's default batching (several
+    position batches of about 1200 evaluations, three in flight on their own streams, the
+    object gradient tiled over 32 x 32 tiles that gather many overlapping patches), at a
+    near-truth evaluation point: all predicted frames, the loss and the whole gradient
+    against the oracle."""
+    from paper_2311_14780_gb300 import pack_objects, plan_for
+    taps = orc.remap_taps(w.F, w.geom.z, w.geom.det_pixel, w.geom.tilt_rad) if w.geom.remap else None
+    O_e, P_e = syn.near_truth(w, seed=seed)
+    O0 = [as_c64_roundtrip(o) for o in O_e]
+    P0 = as_c64_roundtrip(P_e)
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, None, None, taps), seed)
+    eps = syn.default_eps(Ih)
+    plan = plan_for(w, eps=eps)
+    O = pack_objects(O0, dev)
+    P = c64(P0, dev)
+    Im = torch.as_tensor(Ih, device=dev).contiguous()
+    Ip = plan.forward(O, P).cpu().numpy()
+    launches_fwd = plan.last_launches
+    La, gO, gP = plan.adjoint(O, P, Im)
+    Lg = float(plan.loss(O, P, Im).item())
+    status = plan.status()
+    plan.close()
+    Ir = orc.predict(O0, P0, w.pos, None, None, taps)
+    Lr, gOr, gPr = orc.gradient(O0, P0, w.pos, Ih, w.loss, eps, None, None, None, taps)
+    gOr = np.concatenate([g.reshape(-1) for g in gOr])
+    gO, gP = gO.cpu().numpy(), gP.cpu().numpy()
+    return dict(I=rel(Ip, Ir), I_max=max_rel_frames(Ip, Ir), L=abs(Lg - Lr) / abs(Lr),
+                La=abs(float(La.item()) - Lr) / abs(Lr), gO=rel(gO, gOr), gP=rel(gP, gPr), gO_max=max_rel(gO, gOr),
+                gP_max=max_rel(gP, gPr), status=status, launches_fwd=launches_fwd)
+
+
+@pytest.mark.slow
+def test_config2_all_positions_default_batching(dev):
+    """Config 2 at full size with all 400 positions in one call (four position batches, three
+    in flight), not a position subset: every frame, the loss and the whole gradient."""
+    err = _full_size_all_positions(dev, syn.config2(), seed=12)
+    assert err["launches_fwd"] >= 3 * 3, err        # row pass, column pass, loss per batch: several batches
+    assert_ok(err)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("F,M,L", [(512, 1, 1), (128, 8, 5)])
+def test_config3_points_all_positions_default_batching(dev, F, M, L):
+    """Sweep points with the largest frames (512^2, one field per position: many positions per
+    batch) and the most fields (128^2 x 8 modes x 5 wavelengths: forty fields per position),
+    all 400 positions under the default batching."""
+    err = _full_size_all_positions(dev, syn.config3(F, M, L), seed=F + 10 * M + L)
+    assert_ok(err)
 
 
 @pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 8, 16, 17, 20, 32, 64, 68, 192, 256, 288, 512])
@@ -380,9 +466,13 @@ def _sigma_bg_errors(case, plan, frames=None):
                                          case.bg, case.mask, case.taps, frames)
     _, gOr, gPr = case.oracle_grad(frames)
     gOr = np.concatenate([g.reshape(-1) for g in gOr])
-    return dict(L=abs(float(La.item()) - Lr) / abs(Lr), gO=rel(gO.cpu().numpy(), gOr), gP=rel(gP.cpu().numpy(), gPr),
-                gs=rel(gs.cpu().numpy(), gsr), gb=rel(gb.cpu().numpy(), gbr), gs_gpu=gs.cpu().numpy(),
-                status=plan.status())
+    got = dict(gO=gO.cpu().numpy(), gP=gP.cpu().numpy(), gs=gs.cpu().numpy(), gb=gb.cpu().numpy())
+    ref = dict(gO=gOr, gP=gPr, gs=gsr, gb=gbr)
+    e = dict(L=abs(float(La.item()) - Lr) / abs(Lr), gs_gpu=got["gs"], status=plan.status())
+    for k in got:
+        e[k] = rel(got[k], ref[k])
+        e[k + "_max"] = max_rel(got[k], ref[k])
+    return e
 
 
 @pytest.mark.parametrize("remap,loss,mask_kind", [(True, "poisson", "frame"), (False, "amplitude", None),
@@ -395,7 +485,7 @@ def test_sigma_background_gradients(dev, remap, loss, mask_kind):
     e = _sigma_bg_errors(case, plan)
     assert e["status"] == 0 and e["L"] < TOL_L, e
     for k in ("gO", "gP", "gs", "gb"):
-        assert e[k] < TOL_G, (k, e)
+        assert e[k] < TOL_G and e[k + "_max"] < TOL_G_MAX, (k, e)
     plan.close()
 
 
@@ -413,7 +503,7 @@ def test_sigma_background_gradients_batches_and_subset(dev, F):
             e = _sigma_bg_errors(case, plan, fr)
             assert e["status"] == 0 and e["L"] < TOL_L, (kw, fr, e)
             for k in ("gO", "gP", "gs", "gb"):
-                assert e[k] < TOL_G, (kw, fr, k, e)
+                assert e[k] < TOL_G and e[k + "_max"] < TOL_G_MAX, (kw, fr, k, e)
             if fr is not None:
                 outside = np.setdiff1d(np.arange(w.J), fr)
                 assert np.all(e["gs_gpu"][outside] == 0.0)
@@ -498,6 +588,31 @@ def test_step_updates_sigma_and_background(dev, device_counter):
     plan.close()
 
 
+def test_step_host_matches_step(dev):
+    """ptycho_step_host (measured patterns in pinned host memory, copied on the stream; the loss
+    copied back to the host) takes exactly the step ptycho_step takes on device data."""
+    from paper_2311_14780_gb300 import AdamState
+    w = syn.tiny_workload(F=64, L=2, M=2, n_side=3, step=10, seed=38, remap=True, loss="poisson")
+    case = Case(w, dev, z=strong_z(64), seed=3)
+    plan = case.plan()
+    s1, s2 = AdamState(plan, 1e-2, 1e-1), AdamState(plan, 1e-2, 1e-1)
+    O1, P1 = case.O.clone(), case.P.clone()
+    O2, P2 = case.O.clone(), case.P.clone()
+    host = torch.as_tensor(case.Ih).contiguous().pin_memory()
+    staging = torch.full_like(case.Im, float("nan"))
+    l1 = torch.zeros(1, dtype=torch.float64, device=dev)
+    l2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    lh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        plan.step(s1, O1, P1, case.Im, loss_out=l1)
+        plan.step_host(s2, O2, P2, host, staging, l2, lh)
+        torch.cuda.synchronize()
+        assert float(lh.item()) == float(l1.item()) == float(l2.item())
+    assert torch.equal(staging, case.Im) and s2.t == s1.t == 2
+    assert torch.equal(O1, O2) and torch.equal(P1, P2)
+    plan.close()
+
+
 def test_autograd_sigma_background(dev):
     """torch.autograd through sigma and bg: a directional derivative vs central differences."""
     from paper_2311_14780_gb300.autograd import ptycho_loss
@@ -545,16 +660,22 @@ def _offset_errors(case, plan, delta, frames=None):
     _, gdr = orc.gradient_delta(*args, d32, case.sigma, case.bg, case.mask, case.taps, frames)
     _, gsr, gbr = orc.gradient_sigma_bg(*args, case.sigma, case.bg, case.mask, case.taps, frames, delta=d32)
     gOr = np.concatenate([g.reshape(-1) for g in gOr])
-    return dict(I=rel(Ip, Ir), L=abs(float(La.item()) - Lr) / abs(Lr), gO=rel(gO.cpu().numpy(), gOr),
-                gP=rel(gP.cpu().numpy(), gPr), gd=rel(gd.cpu().numpy(), gdr), gs=rel(gs.cpu().numpy(), gsr),
-                gb=rel(gb.cpu().numpy(), gbr), gd_gpu=gd.cpu().numpy(), status=plan.status())
+    got = dict(gO=gO.cpu().numpy(), gP=gP.cpu().numpy(), gd=gd.cpu().numpy(), gs=gs.cpu().numpy(),
+               gb=gb.cpu().numpy())
+    ref = dict(gO=gOr, gP=gPr, gd=gdr, gs=gsr, gb=gbr)
+    e = dict(I=rel(Ip, Ir), I_max=max_rel_frames(Ip, Ir), L=abs(float(La.item()) - Lr) / abs(Lr),
+             gd_gpu=got["gd"], status=plan.status())
+    for k in got:
+        e[k] = rel(got[k], ref[k])
+        e[k + "_max"] = max_rel(got[k], ref[k])
+    return e
 
 
 def _assert_offsets_ok(e):
     assert e["status"] == 0, e
-    assert e["I"] < TOL_I and e["L"] < TOL_L, e
+    assert e["I"] < TOL_I and e["L"] < TOL_L and e["I_max"] < TOL_I_MAX, e
     for k in ("gO", "gP", "gd", "gs", "gb"):
-        assert e[k] < TOL_G, (k, e)
+        assert e[k] < TOL_G and e[k + "_max"] < TOL_G_MAX, (k, e)
 
 
 @pytest.mark.parametrize("F", [64, 128, 256, 512])

@@ -223,3 +223,88 @@ def test_graph_replayed_steps_match_eager_steps():
     assert rel(O2.cpu().numpy(), O1.cpu().numpy()) < REL
     assert rel(P2.cpu().numpy(), P1.cpu().numpy()) < REL
     plan.close()
+
+
+def _oracle_request(F, L, M, n_side, seed, dev, iterations):
+    """A small serving request whose measured data come from the oracle's model of the truth
+    (nothing computed on the GPU), with the oracle's view of the same inputs."""
+    from oracle import ptycho_oracle as orc
+    from paper_2311_14780_gb300 import pack_objects
+    from paper_2311_14780_gb300.serve import Request
+    w = syn.tiny_workload(F=F, L=L, M=M, n_side=n_side, step=F // 8, seed=seed, remap=True, loss="poisson")
+    z = F * 15e-6 / 0.5                       # the remap visibly distorts these small frames
+    taps = orc.remap_taps(F, z, w.geom.det_pixel, w.geom.tilt_rad)
+    Ih = syn.poisson_measure(orc.predict(w.O_true, w.P_true, w.pos, None, None, taps), seed)
+    eps = syn.default_eps(Ih)
+    O0 = [np.asarray(o).astype(np.complex64).astype(np.complex128) for o in w.O0]
+    P0 = np.asarray(w.P0).astype(np.complex64).astype(np.complex128)
+    r = Request(f"oracle_F{F}", 0.0, F, L, M, w.J, w.obj_shapes, w.pos, pack_objects(O0, dev),
+                torch.as_tensor(P0, dtype=torch.complex64, device=dev).contiguous(),
+                torch.as_tensor(Ih, device=dev).contiguous(), iterations=iterations, loss="poisson", eps=eps, z=z,
+                lr_O=1e-2, lr_P=1e-2)
+    return r, w, taps, Ih, eps
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_served_sites_follow_the_oracle():
+    """The serving stream's rules in miniature: one site per frame size (128, 256, 512), with
+    different wavelength and mode counts, admitted together and served in mixed ticks (one
+    launch runs an iteration of every site).  After each of three iterations, every site's
+    loss is compared with the oracle's loss at the parameters that iteration started from,
+    and its parameter update with the oracle's Adam step from the same parameters (FP64
+    gradients, moments carried over the same sequence of states).
+
+    Adam normalises each real component by its own gradient history, so a component whose
+    gradient is at the level of FP32 rounding (object pixels under the probe's far tails)
+    moves by +-lr with the sign of that rounding.  The update is therefore compared on the
+    components whose every gradient so far exceeds 1e-3 of its array's largest magnitude,
+    and bounded by the learning rate everywhere."""
+    from oracle import ptycho_oracle as orc
+    from paper_2311_14780_gb300.api import unpack_objects
+    from paper_2311_14780_gb300.serve import Server
+    dev = torch.device("cuda", 0)
+    sites = [_oracle_request(128, 2, 2, 3, 61, dev, 3), _oracle_request(256, 1, 3, 2, 62, dev, 3),
+             _oracle_request(512, 1, 2, 2, 63, dev, 3)]
+    hp = dict(b1=float(np.float32(0.9)), b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)))
+    sv = Server(16 << 30)
+    slots = [sv.admit(s[0]) for s in sites]
+    assert None not in slots
+    ost = [orc.AdamState([tuple(sh) for sh in s[1].obj_shapes], tuple(s[0].P.shape)) for s in sites]
+    keep = [None] * len(sites)          # components whose gradients so far were all well above rounding
+
+    def real(z):
+        return np.stack([z.real, z.imag], -1).reshape(-1)
+
+    for it in range(3):
+        x0 = [([o.cpu().numpy().astype(np.complex128) for o in unpack_objects(s[0].O, s[0].obj_shapes)],
+               s[0].P.cpu().numpy().astype(np.complex128)) for s in sites]
+        assert sv.tick() == len(sites)
+        torch.cuda.synchronize()
+        for k, (r, w, taps, Ih, eps) in enumerate(sites):
+            n_it, loss = sv.status(slots[k])
+            assert n_it == it + 1
+            O_start, P_start = x0[k]
+            Lr, gO, gP = orc.gradient(O_start, P_start, w.pos, Ih, "poisson", eps, None, None, None, taps)
+            assert abs(loss - Lr) <= 1e-5 * abs(Lr), (r.name, it, loss, Lr)
+            st = ost[k]
+            st.t += 1
+            On = [orc.adam_update(O_start[l], gO[l], st.mO[l], st.vO[l], st.t, r.lr_O, **hp) for l in range(w.L)]
+            Pn = orc.adam_update(P_start, gP, st.mP, st.vP, st.t, r.lr_P, **hp)
+            upd_ref = np.concatenate([real(np.concatenate([(a - b).ravel() for a, b in zip(On, O_start)])),
+                                      real((Pn - P_start).ravel())])
+            O_now = [o.cpu().numpy().astype(np.complex128) for o in unpack_objects(r.O, r.obj_shapes)]
+            P_now = r.P.cpu().numpy().astype(np.complex128)
+            upd = np.concatenate([real(np.concatenate([(a - b).ravel() for a, b in zip(O_now, O_start)])),
+                                  real((P_now - P_start).ravel())])
+            g = np.concatenate([real(np.concatenate([x.ravel() for x in gO])), real(gP.ravel())])
+            nO = 2 * sum(x.size for x in gO)
+            big = np.concatenate([np.abs(g[:nO]) > 1e-3 * np.abs(g[:nO]).max(),
+                                  np.abs(g[nO:]) > 1e-3 * np.abs(g[nO:]).max()])
+            keep[k] = big if keep[k] is None else keep[k] & big
+            assert keep[k].sum() > 0.1 * keep[k].size or keep[k].sum() > 1000, (r.name, keep[k].sum())
+            assert rel(upd[keep[k]], upd_ref[keep[k]]) < 1e-4, (r.name, it, rel(upd[keep[k]], upd_ref[keep[k]]))
+            assert np.abs(upd).max() <= 1.01 * max(r.lr_O, r.lr_P) * 3.2, (r.name, it)
+    for s in slots:
+        sv.release(s)
+    sv.close()
