@@ -109,7 +109,8 @@ typedef struct {
   const int32_t* obj_w;     /* [L] object columns, >= F                                 */
   const int32_t* pos;       /* [L][J][2] (row, col) of each patch's top-left corner in
                                wavelength-l object pixels: the integer scan shift s_j of
-                               f2 (Eq. 2).  0 <= row <= obj_h[l] - F, same for col.    */
+                               f2 (Eq. 2).  0 <= row <= obj_h[l] - F, same for col.
+                               Bound at plan creation: a new scan needs a new plan.    */
   const double* lambda;     /* [L] wavelengths in metres (recorded; may be NULL)        */
   double z;                 /* sample-camera distance, metres (88 mm in the paper)      */
   double det_pixel;         /* camera pixel pitch, metres (15 um)                       */
@@ -117,10 +118,11 @@ typedef struct {
   int32_t remap;            /* 1: apply the tilted-plane remap inside f5; 0: identity   */
   int32_t loss;             /* PTYCHO_LOSS_AMPLITUDE, _POISSON or _POISSON_GAUSSIAN     */
   float eps;                /* intensity floor added to I in the loss and its gradient  */
-  int64_t scratch_bytes;    /* FFT scratch budget in bytes; 0 = library default (about 128
-                               evaluations per batch, at most 2 GiB)                  */
+  int64_t scratch_bytes;    /* FFT scratch budget in bytes; 0 = library default (about
+                               1200 evaluations per batch and at least three batches per
+                               call, at most 2 GiB per buffer set)                     */
   int32_t overlap;          /* position batches in flight on separate streams (1..4), each
-                               with its own scratch set; 0 = library default (2)       */
+                               with its own scratch set; 0 = library default (3)       */
   int32_t flags;            /* PTYCHO_FLAG_* variants; 0 = defaults                      */
   int32_t col_groups;       /* mode groups of the column passes (partial intensity sums
                                per position); 0 = library default                       */
@@ -296,6 +298,21 @@ int ptycho_regularise(ptycho_plan_t* plan, const float* O, float mu_l1, float mu
 int ptycho_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, float* sigma,
                 float* bg, const float* I_meas, const uint8_t* mask, int mask_per_frame,
                 const int32_t* batch_idx, int nbatch, double* loss_dev, void* stream);
+
+/* ptycho_step for a caller whose measured patterns and loss live in HOST memory (the paper
+ * keeps its whole dataset resident on the GPU to avoid host-device transfers, Section
+ * "Discussion"; this entry point is the form for data that stay on the host).  On stream:
+ * I_meas_host (HOST, J*F*F floats, camera grid; page-locked memory makes the copy
+ * asynchronous, pageable memory makes this call wait for it) is copied into the caller's
+ * DEVICE buffer I_meas_dev (J*F*F floats), ptycho_step runs on it with the other arguments
+ * as documented there (loss_dev: DEVICE, 1 double, required here), and the loss is copied
+ * into loss_host (HOST, 1 double), valid once the stream has passed this point.  The library
+ * allocates nothing here.  PTYCHO_EINVAL for a NULL plan, I_meas_host, I_meas_dev, loss_dev
+ * or loss_host, or a plan made on another device; PTYCHO_ECUDA when a copy cannot be
+ * issued; otherwise the errors of ptycho_step. */
+int ptycho_step_host(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, float* sigma, float* bg,
+                     const float* I_meas_host, float* I_meas_dev, const uint8_t* mask, int mask_per_frame,
+                     const int32_t* batch_idx, int nbatch, double* loss_dev, double* loss_host, void* stream);
 
 /* Number of kernel launches issued by the most recent compute call on this plan. */
 int64_t ptycho_plan_last_launches(const ptycho_plan_t* plan);

@@ -1,6 +1,8 @@
 // Orchestration of one compute call for a fixed frame size F: loops over position batches
 // and mode chunks and launches the kernels of kernels.cuh on the caller's stream.
 #pragma once
+#include <mutex>
+
 #include "plan.h"
 
 namespace ptycho {
@@ -69,10 +71,18 @@ int launch_cols_s(ptycho_plan& p, bool fwd, bool store, cudaStream_t cs, float2*
   return PTYCHO_OK;
 }
 
+// Raises the dynamic shared-memory limit of every kernel of frame size F on the current device
+// (cudaFuncSetAttribute acts per device), once per device; thread-safe.
 template <int F>
 int prepare_kernels() {
-  static int done = 0;
-  if (done) return PTYCHO_OK;
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PTYCHO_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return PTYCHO_EINVAL;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return PTYCHO_OK;
   const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(k_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
@@ -102,7 +112,7 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = set_cols_smem<F, 0>();
   if (e == cudaSuccess) e = set_cols_smem<F, 4>();
   if (e != cudaSuccess) return PTYCHO_ECUDA;
-  done = 1;
+  done[dev] = true;
   return PTYCHO_OK;
 }
 

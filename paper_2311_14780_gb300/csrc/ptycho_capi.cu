@@ -364,19 +364,17 @@ void build_remap(int F, double z, double p, double alpha, std::vector<int32_t>& 
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+// Looked up once per process (a thread-safe static initialisation).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static int tried = 0;
-  if (!tried) {
-    tried = 1;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -968,6 +966,27 @@ int ptycho_step(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* s
     ++p->last_launches;
   }
   if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
+  return PTYCHO_OK;
+}
+
+int ptycho_step_host(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, float* sigma, float* bg,
+                     const float* I_meas_host, float* I_meas_dev, const uint8_t* mask, int mask_per_frame,
+                     const int32_t* batch_idx, int nbatch, double* loss_dev, double* loss_host, void* stream) {
+  if (!p || !I_meas_host || !I_meas_dev || !loss_dev || !loss_host) return PTYCHO_EINVAL;
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(float) * (size_t)p->J * (size_t)p->F * (size_t)p->F;
+  if (cudaMemcpyAsync(I_meas_dev, I_meas_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    return PTYCHO_ECUDA;
+  }
+  rc = ptycho_step(p, s, O, P, sigma, bg, I_meas_dev, mask, mask_per_frame, batch_idx, nbatch, loss_dev, stream);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(loss_host, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    return PTYCHO_ECUDA;
+  }
   return PTYCHO_OK;
 }
 
