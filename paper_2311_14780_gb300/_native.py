@@ -70,6 +70,8 @@ SIGNATURES = [
     ("ptycho_plan_set_distance", _I, [_VP, ctypes.c_double]),
     ("ptycho_plan_set_offsets", _I, [_VP, _VP]),
     ("ptycho_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
+    ("ptycho_step_host", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP, _VP,
+                              _VP]),
     ("ptycho_plan_status", _I, [_VP, c_int32_p]),
     ("ptycho_plan_profile", _I, [_VP, _I]),
     ("ptycho_plan_profile_read", _I, [_VP, c_double_p, ctypes.POINTER(ctypes.c_int64)]),
@@ -94,7 +96,7 @@ SIGNATURES = [
     ("ptycho_strerror", ctypes.c_char_p, [_I]),
 ]
 
-NUM_KERNELS = 11
+NUM_KERNELS = 13
 _LIB = None
 
 

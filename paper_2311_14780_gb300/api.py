@@ -317,6 +317,33 @@ class Plan:
         state.t = int(st.t)
         return loss_out
 
+    def step_host(self, state: "AdamState", O, P, Imeas_host, Imeas_dev, loss_dev, loss_host, sigma=None, bg=None,
+                  mask=None, batch=None, stream=None):
+        """ptycho_step_host: ``step`` with the measured patterns in host memory (``Imeas_host``,
+        a contiguous float32 CPU tensor, pinned for an asynchronous copy) copied on the stream
+        into ``Imeas_dev`` (device, float32), and the FP64 loss copied from ``loss_dev`` (device)
+        into ``loss_host`` (a float64 CPU tensor, pinned for an asynchronous copy)."""
+        FF = self.F * self.F
+        Or, Pr = self._c64(O, self.numel_O, "O"), self._c64(P, self.numel_P, "P")
+        if Imeas_host.dtype != torch.float32 or Imeas_host.is_cuda or not Imeas_host.is_contiguous() or \
+                Imeas_host.numel() != self.J * FF:
+            raise ValueError(f"Imeas_host: need a contiguous float32 host tensor of {self.J * FF} elements")
+        if loss_host.dtype != torch.float64 or loss_host.is_cuda or loss_host.numel() < 1:
+            raise ValueError("loss_host: need a float64 host tensor")
+        if loss_dev.dtype != torch.float64 or loss_dev.device != self.device:
+            raise ValueError("loss_dev: need a float64 tensor on the plan's device")
+        m, mpf = self._mask(mask)
+        bt, nb = self._batch(batch)
+        st = state.c_struct()
+        rc = _native.lib().ptycho_step_host(self._h_plan, ctypes.byref(st), _ptr(Or), _ptr(Pr),
+                                            _ptr(self._f32(sigma, self.J, "sigma")), _ptr(self._f32(bg, FF, "bg")),
+                                            _ptr(Imeas_host), _ptr(self._f32(Imeas_dev, self.J * FF, "Imeas_dev")),
+                                            _ptr(m), mpf, _ptr(bt), nb, _ptr(loss_dev), _ptr(loss_host),
+                                            _stream_handle(stream))
+        _check(rc, "ptycho_step_host")
+        state.t = int(st.t)
+        return loss_host
+
     def plain_step(self, state: "AdamState", O, P, Imeas, sigma=None, bg=None, mask=None, loss_out=None,
                    stream=None):
         """ptycho_plain_step: the unfused baseline of ``step`` over all positions."""
