@@ -462,18 +462,16 @@ def corrections_block(w, plan, st, O, P, Im, loss, eps, evals, dev, stream, flus
                 "note": "ptycho_tilt_apply of the step's camera patterns (thresholds 4 and 65535) with a table "
                         "built once per geometry (ptycho_tilt_table, FP64, timed separately); L2 flushed before "
                         "each call; frac of measured HBM copy bandwidth"}
-    czt_ms = None
-    if w.F <= 256:
-        # the chirp-z propagator: every wavelength on the first one's object grid (zoom
-        # lambda_1 / lambda_l, the first wavelength's positions for all)
-        lam = np.asarray(w.geom.lambdas, dtype=np.float64)
-        from paper_2311_14780_gb300.api import Plan
-        pos_common = np.repeat(np.asarray(w.pos)[:1], w.L, axis=0)
-        pz = Plan(w.F, w.L, w.M, w.J, w.obj_shapes, pos_common, loss=w.loss, eps=eps, remap=w.geom.remap,
-                  z=w.geom.z, det_pixel=w.geom.det_pixel, tilt_rad=w.geom.tilt_rad, zoom=lam[0] / lam)
-        st_z2 = AdamState(pz, lr_O=1e-3, lr_P=1e-3)
-        czt_ms = timed(lambda: pz.step(st_z2, O2, P2, Im, loss_out=loss), nsteps)
-        pz.close()
+    # the chirp-z propagator: every wavelength on the first one's object grid (zoom
+    # lambda_1 / lambda_l, the first wavelength's positions for all)
+    lam = np.asarray(w.geom.lambdas, dtype=np.float64)
+    from paper_2311_14780_gb300.api import Plan
+    pos_common = np.repeat(np.asarray(w.pos)[:1], w.L, axis=0)
+    pz = Plan(w.F, w.L, w.M, w.J, w.obj_shapes, pos_common, loss=w.loss, eps=eps, remap=w.geom.remap,
+              z=w.geom.z, det_pixel=w.geom.det_pixel, tilt_rad=w.geom.tilt_rad, zoom=lam[0] / lam)
+    st_z2 = AdamState(pz, lr_O=1e-3, lr_P=1e-3)
+    czt_ms = timed(lambda: pz.step(st_z2, O2, P2, Im, loss_out=loss), nsteps)
+    pz.close()
     corrections = {
         "steps": nsteps,
         "object_probe": {"ms_per_step": base_ms, "evals_per_s": evals / (base_ms / 1e3)},

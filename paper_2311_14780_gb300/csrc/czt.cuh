@@ -11,10 +11,12 @@
 // The convolution runs as an N-point FFT, a product with the kernel's spectrum Hhat (one per
 // wavelength, built in FP64 on the host) and an inverse FFT.  Z^H uses the conjugate chirps.
 //
-// A vector of F values sits with T = N1 threads (layout I: thread t holds n = t + N1*n2); the
-// N-point transform uses the same threads with 2F/N1 = 32 values each, the data in the first
-// half and zeros in the second, so F = 64, 128 and 256 are supported (F = 512 would need 64
-// values per thread).
+// A vector of F values sits with T = N1 = F/16 threads (layout I: thread t holds n = t + N1*n2,
+// 16 values); the N-point transform uses the same threads with 2F/N1 = 32 values each, the data
+// in the first half and zeros in the second.  At F = 64, 128 and 256 N1 is the register FFT's
+// (4, 8, 16); at F = 512 a vector takes a whole warp (N1 = 32, where the register FFT's 512-point
+// rows use 16 threads of 32 values), so that the 1024-point transform is 32 x 32 and still fits
+// 32 values per thread.
 #pragma once
 #include "kernels.cuh"
 
@@ -68,7 +70,7 @@ __device__ __forceinline__ void fftn_inv_O2I(float2 (&x)[N2], int t, float2* xc,
 }
 
 template <int F> struct CztShape {
-  static constexpr int N1 = FftShape<F>::N1;
+  static constexpr int N1 = F / 16;                   // threads per vector (FftShape<F>::N1 up to 256)
   static constexpr int NF = F / N1;                   // values per thread of an F-vector (16)
   static_assert(2 * NF == kCztV, "the chirp-z transform needs F/N1 = 16");
   static constexpr int xch = kCztV * (N1 + 1);        // exchange elements per vector

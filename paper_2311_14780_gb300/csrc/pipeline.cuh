@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "plan.h"
+#include "resident.cuh"
 
 namespace ptycho {
 
@@ -103,14 +104,16 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_cols<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_cols<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
-  if constexpr (F <= 256) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztRowCfg<F>::smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_col_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztColCfg<F>::smem_fwd);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_col_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztColCfg<F>::smem_adj);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztRowAdjCfg<F>::smem);
-  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_row_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztRowCfg<F>::smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_col_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztColCfg<F>::smem_fwd);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_col_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztColCfg<F>::smem_adj);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_czt_row_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, CztRowAdjCfg<F>::smem);
   if (e == cudaSuccess) e = set_cols_smem<F, 0>();
   if (e == cudaSuccess) e = set_cols_smem<F, 4>();
+  if constexpr (ResSupported<F>::value) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg<F>::smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res_adj<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg<F>::smem);
+  }
   if (e != cudaSuccess) return PTYCHO_ECUDA;
   done[dev] = true;
   return PTYCHO_OK;
@@ -139,7 +142,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const bool col_staged = p.col_staged && p.nchunks == 1;
   const bool fwd_l = p.fwd_l && p.nchunks == 1 && !shifted;
   const bool narrow = (p.flags & PTYCHO_FLAG_NARROW_COLUMNS) != 0;
-  const int nsplit = adj_l ? p.nsplit_adj : 1;
+  // frame-resident passes (F <= 128, PTYCHO_FLAG_RESIDENT_FRAMES): fields stay in one block's
+  // shared memory
+  const bool res = ResSupported<F>::value && p.res && !shifted && !p.czt && p.nchunks == 1 && !obj_atomic;
+  const int nsplit = res ? p.nsplit_res : adj_l ? p.nsplit_adj : 1;
   float2* gPs = nsplit > 1 ? p.d_gPs : c.gP;
 
   KArgs a{};
@@ -151,8 +157,8 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   a.sigma = c.sigma;
   a.tw = p.d_tw;
   a.C = p.C;
-  a.MG = p.MG;
-  a.G = p.G;
+  a.MG = res ? p.MG_res : p.MG;
+  a.G = res ? p.G_res : p.G;
   a.status = p.d_status;
 
   LossArgs la{};
@@ -171,12 +177,12 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   la.sig_part = grad && c.g_sigma ? p.d_sig_part : nullptr;
   la.I_pred = c.kind == CallKind::Forward ? c.I_pred : nullptr;
   la.remap = p.remap;
-  la.Gsum = p.G;
+  la.Gsum = a.G;
   la.tap_dz = p.d_tap_dz;
   la.z_part = grad && c.g_z ? p.d_z_part : nullptr;
 
   CztArgs ct{p.d_czt_chirp, p.d_czt_hf, p.d_czt_ha, p.d_czt_tw2};
-  if (p.czt && (F > 256 || p.nchunks != 1 || p.d_delta)) return PTYCHO_EUNSUPPORTED;
+  if (p.czt && (p.nchunks != 1 || p.d_delta)) return PTYCHO_EUNSUPPORTED;
   AdjArgs aa{};
   aa.D = p.d_D;
   aa.rt_ptr = p.d_rt_ptr;
@@ -199,7 +205,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
   const int col_adj_smem = ColCfg<F>::smem_xch + F * ColCfg<F>::W * (int)sizeof(float);
   const int nbatches = (c.nbatch + p.B - 1) / p.B;
   const int nsets = p.nsets < nbatches ? p.nsets : nbatches;
-  const long long set_S = (long long)p.B * p.C * FF, set_I = (long long)p.B * p.G * FF, set_F = (long long)p.B * FF;
+  const long long set_S = (long long)p.B * p.C * FF, set_I = (long long)p.B * a.G * FF, set_F = (long long)p.B * FF;
   cudaStream_t streams[ptycho_plan::kMaxSets] = {st};
   for (int i = 1; i < nsets; ++i) streams[i] = p.side[i - 1];
   if (nsets > 1) {                                    // the side streams follow the caller's work so far
@@ -255,10 +261,18 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       PTY_LAUNCH(p, kShift, cs, launch_pdl(k_shift_rows<F, true, false>, rgrid, row_blk, RowCfg<F>::smem, cs, c.O, a, sh));
       a.patch = Pt;
     }
-    for (int ch = 0; ch < p.nchunks; ++ch) {
+    if constexpr (ResSupported<F>::value) {
+      if (res) {                                      // all modes of the batch, frames on chip
+        a.chunk_base = 0;
+        a.chunk_len = LM;
+        PTY_LAUNCH(p, kResFwd, cs, launch_pdl(k_res_fwd<F>, dim3(a.nb, a.G), ResCfg<F>::threads, ResCfg<F>::smem, cs,
+                                              c.O, c.P, Ip, a));
+      }
+    }
+    for (int ch = 0; ch < p.nchunks && !res; ++ch) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
-      if constexpr (F <= 256) {
+      {
         if (p.czt) {                                  // chirp-z propagator
           PTY_LAUNCH(p, kRowFwd, cs, launch_pdl(k_czt_row_fwd<F>, dim3(F / CztRowCfg<F>::RPB, p.L, a.nb),
                                                 CztRowCfg<F>::threads, CztRowCfg<F>::smem, cs, c.O, c.P, S, a, ct));
@@ -302,7 +316,21 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       a.chunk_base = ch * p.C;
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       const dim3 col_grid(F / ColCfg<F>::W, p.G, a.nb);
-      if constexpr (F <= 256) {
+      if constexpr (ResSupported<F>::value) {
+        if (res) {                                    // Psi recomputed on chip, chi, both gradients
+          if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_radj[(k - 1) % nsets], 0) != cudaSuccess)
+            return PTYCHO_ECUDA;
+          PTY_LAUNCH(p, kResAdj, cs, launch_pdl(k_res_adj<F>, dim3(LM, nsplit), ResCfg<F>::threads, ResCfg<F>::smem, cs,
+                                                c.O, c.P, S, gPs, (long long)p.P_numel, a, aa, nsplit));
+          if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+          if (nsets > 1 && k > 0 && cudaStreamWaitEvent(cs, p.ev_og[(k - 1) % nsets], 0) != cudaSuccess)
+            return PTYCHO_ECUDA;
+          PTY_LAUNCH(p, kObjGrad, cs, launch_pdl(k_obj_grad<F>, dim3(max_tiles, p.L), 256, 0, cs, S, c.gO, a));
+          if (nsets > 1 && cudaEventRecord(p.ev_og[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
+          continue;
+        }
+      }
+      {
         if (p.czt) {                                  // chirp-z propagator
           PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_czt_col_adj<F>, dim3(F / CztColCfg<F>::W, p.G, a.nb),
                                                 CztColCfg<F>::threads, CztColCfg<F>::smem_adj, cs, S, a, aa, ct));

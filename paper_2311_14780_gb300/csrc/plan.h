@@ -42,6 +42,9 @@ struct ptycho_plan {
   // staged column passes (k_col_fwd_s / k_col_adj_s): one block per W columns of a position
   // runs over all its modes, so the column passes leave a single intensity slice (G = 1)
   int col_staged = 0;
+  // frame-resident passes (F <= 128, resident.cuh): the forward over G_res mode groups of MG_res
+  // modes per position, the adjoint over nsplit_res position splits per probe mode
+  int res = 0, G_res = 1, MG_res = 1, nsplit_res = 1;
   long long scratch_budget = 0;
 
   // nsets buffer sets let consecutive position batches overlap: batch k runs on stream
@@ -134,7 +137,7 @@ struct CallArgs {
 
 // Kernel kinds reported by ptycho_plan_profile_read (order matches PTYCHO_K_* in ptycho.h).
 enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLossReduce, kAdam, kRemapAdj, kShift, kReg,
-                  kNumKinds };
+                  kResFwd, kResAdj, kNumKinds };
 
 // Records the start event of a profiled launch (no-op unless profiling); returns the pair index.
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);

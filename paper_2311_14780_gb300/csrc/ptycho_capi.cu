@@ -225,9 +225,10 @@ int load_czt(ptycho_plan* p, const double* zoom) {
   const int F = p->F, N = 2 * F, L = p->L;
   int N1 = 0;
   switch (F) {
-    case 64: N1 = ptycho::FftShape<64>::N1; break;
-    case 128: N1 = ptycho::FftShape<128>::N1; break;
-    default: N1 = ptycho::FftShape<256>::N1; break;
+    case 64: N1 = ptycho::CztShape<64>::N1; break;
+    case 128: N1 = ptycho::CztShape<128>::N1; break;
+    case 256: N1 = ptycho::CztShape<256>::N1; break;
+    default: N1 = ptycho::CztShape<512>::N1; break;
   }
   std::vector<float2> chirp((size_t)L * F), hf((size_t)L * N), ha((size_t)L * N), tw2((size_t)N);
   std::vector<double> hr(N), hi(N);
@@ -458,7 +459,6 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
   if (g->zoom) {
     for (int l = 0; l < g->L; ++l)
       if (!(g->zoom[l] > 0.0 && g->zoom[l] <= 4.0)) return PTYCHO_EINVAL;
-    if (g->F > 256) return PTYCHO_EUNSUPPORTED;       // the 2F-point transform needs F/N1 = 16
   }
   if (!(g->eps >= 0.f) || !isfinite(g->eps)) return PTYCHO_EINVAL;
   if (g->remap && !(g->z > 0.0 && g->det_pixel > 0.0 && isfinite(g->tilt_rad) && fabs(g->tilt_rad) < kPi / 2))
@@ -484,7 +484,7 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
   p->loss_kind = g->loss;
   p->read_var = g->loss == PTYCHO_LOSS_POISSON_GAUSSIAN ? g->read_noise_var : 0.f;
   p->flags = g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_OBJ_GRAD_ATOMIC | PTYCHO_FLAG_NARROW_COLUMNS |
-                         PTYCHO_FLAG_NO_PDL);
+                         PTYCHO_FLAG_NO_PDL | PTYCHO_FLAG_RESIDENT_FRAMES);
   // measured: recomputing the column DFT beats keeping Psi from F = 256 up
   if (!(g->flags & (PTYCHO_FLAG_RECOMPUTE_COLUMNS | PTYCHO_FLAG_KEEP_PSI)) && g->F >= 256)
     p->flags |= PTYCHO_FLAG_RECOMPUTE_COLUMNS;
@@ -588,6 +588,26 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
     }
   }
 
+  // frame-resident passes (F <= 128, opt-in; measured slower than the scratch passes): all
+  // modes of a position in one chunk; the forward's blocks (position, mode group) and the
+  // adjoint's (probe mode, position split) aim at two waves of resident blocks (one block per SM
+  // at F = 128, two at F = 64); each split sums its probe gradient into a buffer of its own
+  // (bounded to 512 MB in all)
+  if (F <= 128 && p->store && !g->zoom && (g->flags & PTYCHO_FLAG_RESIDENT_FRAMES) &&
+      !(g->flags & PTYCHO_FLAG_OBJ_GRAD_ATOMIC)) {
+    const long long per_sm = F <= 64 ? 2 : 1;
+    const long long want = 2 * per_sm * p->sms;
+    long long Gr = (want + p->B - 1) / p->B;
+    Gr = std::max<long long>(1, std::min<long long>(Gr, LM));
+    p->MG_res = (int)((LM + Gr - 1) / Gr);
+    p->G_res = (int)((LM + p->MG_res - 1) / p->MG_res);
+    long long ns = (want + LM - 1) / LM;
+    ns = std::max<long long>(1, std::min<long long>(ns, p->B));
+    while (ns > 1 && ns * p->P_numel * (long long)sizeof(float2) > (512ll << 20)) --ns;
+    p->nsplit_res = (int)ns;
+    p->res = 1;
+  }
+
   // chirp-z propagator: its own passes (the per-mode row adjoint, the mode-group columns with
   // the column transform recomputed in the adjoint); all modes of a position in the scratch
   if (g->zoom) {
@@ -624,7 +644,7 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
       rc = PTYCHO_ECUDA;
   }
   rc = rc ? rc : dalloc(p, &p->d_S, (long long)p->nsets * p->B * p->C * FF);
-  rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->nsets * p->B * p->G * FF);
+  rc = rc ? rc : dalloc(p, &p->d_Ipart, (long long)p->nsets * p->B * std::max(p->G, p->res ? p->G_res : 1) * FF);
   rc = rc ? rc : dalloc(p, &p->d_D, (long long)p->nsets * p->B * FF);
   rc = rc ? rc : dalloc(p, &p->d_loss_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
   rc = rc ? rc : dalloc(p, &p->d_sig_part, (long long)g->J * (FF / (ptycho::kLossThreads * ptycho::kLossPx)));
@@ -633,7 +653,10 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
   rc = rc ? rc : dalloc(p, &p->d_gbg, FF);
   rc = rc ? rc : dalloc(p, &p->d_gO, p->O_numel);
   rc = rc ? rc : dalloc(p, &p->d_gP, p->P_numel);
-  if (p->adj_l_ok && p->nsplit_adj > 1) rc = rc ? rc : dalloc(p, &p->d_gPs, (long long)p->nsplit_adj * p->P_numel);
+  {
+    const int ns = std::max(p->adj_l_ok ? p->nsplit_adj : 1, p->res ? p->nsplit_res : 1);
+    if (ns > 1) rc = rc ? rc : dalloc(p, &p->d_gPs, (long long)ns * p->P_numel);
+  }
   rc = rc ? rc : dalloc(p, &p->d_status, 1);
   if (!rc && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = PTYCHO_ECUDA;
   if (rc) { free_plan(p); return rc; }
@@ -734,7 +757,7 @@ int ptycho_plan_profile_read(ptycho_plan_t* p, double* ms, int64_t* launches) {
 
 const char* ptycho_kernel_name(int kind) {
   static const char* names[] = {"row_fwd", "col_fwd", "loss", "col_adj", "row_adj", "obj_grad", "loss_reduce", "adam",
-                                "remap_adj", "shift", "regulariser"};
+                                "remap_adj", "shift", "regulariser", "res_fwd", "res_adj"};
   return (kind >= 0 && kind < ptycho::kNumKinds) ? names[kind] : "unknown";
 }
 
