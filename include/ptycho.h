@@ -80,6 +80,10 @@ extern "C" {
  *   in registers and the next position's object rows prefetched (cp.async).  Measured slower
  *   than the default one-position-per-block pass.
  * NO_PDL: launch without programmatic dependent launch.
+ * ROW_ADJ_PROBE_L2 / ROW_ADJ_PROBE_SMEM: the fused row adjoint reads its probe rows through
+ *   L1/L2 (and is compiled for two blocks of at most 160 threads per SM) / holds them in shared
+ *   memory for the batch.  Default: L1/L2 at F = 512 when T*M*rpb <= 160 (measured 1-3 % faster
+ *   there), shared memory otherwise.  PROBE_SMEM wins when both are given.
  * RESIDENT_FRAMES: at F <= 128, frame-resident passes instead of the scratch passes: one
  *   block holds a whole F x F field in shared memory, so exit waves and spectra never leave
  *   the SM; the forward writes only the per-position intensity, the adjoint recomputes Psi on
@@ -99,6 +103,8 @@ extern "C" {
 #define PTYCHO_FLAG_FUSED_ROW_FWD 256
 #define PTYCHO_FLAG_NO_PDL 512
 #define PTYCHO_FLAG_RESIDENT_FRAMES 1024
+#define PTYCHO_FLAG_ROW_ADJ_PROBE_L2 2048
+#define PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM 4096
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */

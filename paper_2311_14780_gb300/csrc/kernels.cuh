@@ -972,9 +972,13 @@ k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
 // ---------------------------------------------------------------------------------------
 constexpr int kRowAdjLSmemMax = 200 * 1024;       // dynamic shared memory cap of k_row_adj_l / k_row_fwd_l
 template <int F>
-__host__ __device__ constexpr int row_adj_l_smem(int M, int rpb) {
-  return (M * rpb * F + 2 * M * rpb * Xch<F>::region_rows + 2 * rpb * F) * (int)sizeof(float2);
+__host__ __device__ constexpr int row_adj_l_smem(int M, int rpb, bool probe_l2 = false) {
+  return ((probe_l2 ? 0 : M * rpb * F) + 2 * M * rpb * Xch<F>::region_rows + 2 * rpb * F) * (int)sizeof(float2);
 }
+// Variant of k_row_adj_l whose probe rows are read through L1/L2 instead of being held in
+// shared memory: at F = 512 with 10 modes that frees 40 KB per block, and the block (at most
+// kRowAdjL2Threads threads) is compiled for two blocks per SM instead of one.
+constexpr int kRowAdjL2Threads = 160;
 
 // Next position of this split after b whose index is valid, or -1 (uniform over the block).
 __device__ __forceinline__ int next_pos(const int2* spos, int b, int nb, int nsplit) {
@@ -993,8 +997,8 @@ __device__ __forceinline__ void prefetch_orows(const float2* __restrict__ Ol, in
   }
 }
 
-template <int F>
-__global__ void __launch_bounds__(256, (F <= 256 ? 2 : 1))
+template <int F, bool PL2>
+__global__ void __launch_bounds__(PL2 ? kRowAdjL2Threads : 256, (F <= 256 || PL2 ? 2 : 1))
 k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
             float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
   pdl_wait();
@@ -1004,8 +1008,8 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
   __shared__ int2 spos[kMaxB];
   __shared__ float ssig[kMaxB];
   const int M = a.M, V = M * rpb;
-  float2* Psm = smem;                                 // [V][F]    probe rows
-  float2* Sst = Psm + V * F;                          // [2][V][RR] scratch rows; the current buffer
+  float2* Psm = smem;                                 // [V][F]    probe rows (not with PL2)
+  float2* Sst = Psm + (PL2 ? 0 : V * F);              // [2][V][RR] scratch rows; the current buffer
                                                       //   is also the FFT exchange and the mode-sum area
   float2* Ost = Sst + 2 * V * RR;                     // [2][rpb][F] object rows
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
@@ -1015,8 +1019,8 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
   const int cm = l * M + m - a.chunk_base;
   const int slot0 = l * M - a.chunk_base;             // slot of the mode sum
   stage_batch(a, l, spos, ssig);
-  {
-    const float2* Prow = P + ((long long)(l * M + m) * F + r) * F;
+  const float2* Prow = P + ((long long)(l * M + m) * F + r) * F;
+  if constexpr (!PL2) {
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) Psm[vec * F + t + N1 * n2] = __ldg(Prow + t + N1 * n2);
   }
@@ -1059,7 +1063,8 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
       const float2 gp = cconjmul(orow[c], v[n2]);                       // conj(p) chi
       acc[n2].x = fmaf(s, gp.x, acc[n2].x);
       acc[n2].y = fmaf(s, gp.y, acc[n2].y);
-      reg[c] = cscale(cconjmul(Psm[vec * F + c], v[n2]), s);            // conj(sigma P) chi
+      const float2 pv = PL2 ? __ldg(Prow + c) : Psm[vec * F + c];
+      reg[c] = cscale(cconjmul(pv, v[n2]), s);                          // conj(sigma P) chi
     }
     __syncthreads();
     float2* dst = S + (((long long)b * a.C + slot0) * F + row0) * F;      // the block's rpb rows, contiguous

@@ -97,7 +97,8 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_fwd);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_fwd_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
@@ -368,10 +369,16 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
         return PTYCHO_ECUDA;
       if (adj_l) {
         constexpr int T = FftShape<F>::N1;
-        PTY_LAUNCH(p, kRowAdj, cs,
-                   launch_pdl(k_row_adj_l<F>, dim3(F / p.rpb_adj, p.L, nsplit), T * p.M * p.rpb_adj,
-                              row_adj_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, gPs, (long long)p.P_numel, a,
-                              p.rpb_adj, nsplit));
+        if (p.adj_l_pl2)
+          PTY_LAUNCH(p, kRowAdj, cs,
+                     launch_pdl(k_row_adj_l<F, true>, dim3(F / p.rpb_adj, p.L, nsplit), T * p.M * p.rpb_adj,
+                                row_adj_l_smem<F>(p.M, p.rpb_adj, true), cs, c.O, c.P, S, gPs, (long long)p.P_numel,
+                                a, p.rpb_adj, nsplit));
+        else
+          PTY_LAUNCH(p, kRowAdj, cs,
+                     launch_pdl(k_row_adj_l<F, false>, dim3(F / p.rpb_adj, p.L, nsplit), T * p.M * p.rpb_adj,
+                                row_adj_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, gPs, (long long)p.P_numel, a,
+                                p.rpb_adj, nsplit));
         if (nsets > 1 && cudaEventRecord(p.ev_radj[k % nsets], cs) != cudaSuccess) return PTYCHO_ECUDA;
         if (shifted) {                                // adjoint shift of the mode-summed patch gradients
           const dim3 rgrid(F / RowCfg<F>::RPB, p.L, a.nb), cgrid(F / ColCfg<F>::W, p.L, a.nb);

@@ -144,11 +144,12 @@ def strong_z(F):
     return F * 15e-6 / 0.5
 
 
-@pytest.mark.parametrize("flags", [0, 32])
+@pytest.mark.parametrize("flags", [0, 32, 4096])
 def test_fused_row_adjoint_at_512_with_eight_modes(dev, flags):
     """F = 512 with 8 modes takes the fused row adjoint (all modes of a wavelength per block,
-    object-gradient rows summed over the modes in shared memory); flag 32 forces the per-mode
-    kernel.  Several position batches and splits."""
+    object-gradient rows summed over the modes in shared memory; probe rows through L1/L2);
+    flag 32 forces the per-mode kernel, flag 4096 the variant that holds the probe rows in
+    shared memory.  Several position batches and splits."""
     w = syn.tiny_workload(F=512, L=1, M=8, n_side=3, step=64, seed=77, remap=True, loss="poisson",
                           with_sigma=True, with_bg=True)
     case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=12)
@@ -442,7 +443,7 @@ def test_config3_points_all_positions_default_batching(dev, F, M, L):
 RESIDENT_FRAMES = 1024
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 8, 16, 17, 20, 32, 64, 68, 192, 256, 288, 512, 1024])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 8, 16, 17, 20, 32, 64, 68, 192, 256, 288, 512, 1024, 2048])
 @pytest.mark.parametrize("F", [64, 128, 256])
 def test_pipeline_variants(dev, flags, F):
     """Recompute-the-columns, atomic object-gradient, keep-Psi, TMA-staged columns (and plain
