@@ -89,6 +89,8 @@ def parse():
                          "(default: 5 at 512^2, 20 otherwise; 0 = skip)")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the reduced serving stream appended to the default line (0 = none)")
+    ap.add_argument("--serve-mode", type=int, default=0,
+                    help="serving tick: 0 = one launch per pass over all sites, 1 = one child graph per site")
     ap.add_argument("--tick-evals", type=int, default=32768,
                     help="config5: admit while the active sites' evaluations per tick stay within this (0 = no cap)")
     return ap.parse_args()
@@ -633,7 +635,8 @@ def run_ours(args, rank: int, world: int):
         sargs = copy.copy(args)
         sargs.requests = args.serving_requests
         served, plain_reqs = serving_requests(sargs, dev)
-        s_sum = serve_stream(served, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None)
+        s_sum = serve_stream(served, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None,
+                             mode=args.serve_mode)
         p_sum = plain_stream(plain_reqs)
         p_sum["final_loss_rel_diff_max"] = max(abs(a.final_loss - b.final_loss) / max(abs(b.final_loss), 1e-300)
                                                for a, b in zip(served, plain_reqs))
@@ -701,7 +704,8 @@ def run_serving(args, rank: int, world: int):
     clocks = ClockSampler(local)
     time.sleep(0.2)
     clocks.mark_start()
-    s_sum = serve_stream(served, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None)
+    s_sum = serve_stream(served, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None,
+                             mode=args.serve_mode)
     clocks.mark_end()
     clk = clocks.stop()
     p_sum = None

@@ -356,14 +356,25 @@ int ptycho_plain_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float
  * Multi-site serving (continuous batching).  The paper reconstructs one dataset at a time;
  * this serves many reconstructions ("sites") of different F, J, L, M at once on one GPU.
  * Each admitted site keeps its plan, Adam moments (zero at admission), a device step
- * counter and its loss resident, and owns a CUDA graph of one iteration (ptycho_step over
- * all its positions) captured at admission.  ptycho_server_tick runs one iteration of every
- * active site as a single graph launch whose per-site branches have no dependencies, so the
- * sites' kernels overlap on the device.  Sites are admitted between ticks while the HBM
- * budget allows (their plan, moments and the caller's resident O, P, I_meas and mask count
- * against it) and give their memory back with ptycho_server_release.  Results of a site
- * do not depend on the other sites in the mix (no shared buffers, fixed-order reductions).
- * Host-driven: no kernel waits on another. */
+ * counter and its loss resident.  ptycho_server_tick runs one iteration of every active
+ * site (forward, loss, adjoint, gradients, Adam over all its positions) as a single graph
+ * launch, in one of two forms:
+ *   PTYCHO_SERVE_SHARED_LAUNCHES (default): per frame size and per round of position batches,
+ *     each pass of the pipeline is ONE kernel launch over the current batch of every active
+ *     site of that frame size (a device work table assigns each block to a site); one launch
+ *     each then reduces every site's loss, advances its step counter and runs its Adam.  The
+ *     graph and tables are rebuilt when the active set changes (that rebuild synchronises the
+ *     device).  These sites take the default pipeline variants and one scratch set: a geometry
+ *     with flags or a zoom is rejected (PTYCHO_EUNSUPPORTED).
+ *   PTYCHO_SERVE_SITE_GRAPHS: each site's own iteration graph (its plan's pipeline) is captured
+ *     at admission and a tick launches one child-graph node per active site with no edges
+ *     between them, so the sites' kernels overlap on the device.
+ * Sites are admitted between ticks while the HBM budget allows (their plan, moments and the
+ * caller's resident O, P, I_meas and mask count against it) and give their memory back with
+ * ptycho_server_release.  Results of a site do not depend on the other sites in the mix (no
+ * shared buffers, per-site fixed-order reductions).  Host-driven: no kernel waits on another. */
+#define PTYCHO_SERVE_SHARED_LAUNCHES 0
+#define PTYCHO_SERVE_SITE_GRAPHS 1
 typedef struct ptycho_server ptycho_server_t;
 
 typedef struct {
@@ -383,7 +394,7 @@ int ptycho_server_create(int64_t hbm_budget_bytes, int32_t max_sites, ptycho_ser
 int ptycho_server_destroy(ptycho_server_t* server);
 /* Validates and plans a site, checks the budget (PTYCHO_EBUSY when it does not fit or no
  * slot is free; nothing stays allocated then), allocates its state and captures its
- * iteration graph.  *slot receives the site's slot.  Synchronous. */
+ * iteration graph (per-site form).  *slot receives the site's slot.  Synchronous. */
 int ptycho_server_admit(ptycho_server_t* server, const ptycho_geom_t* geom, const ptycho_site_t* site,
                         int32_t* slot);
 /* Enqueues one iteration of every site that has iterations left, as one graph launch on
@@ -396,6 +407,9 @@ int ptycho_server_site_status(ptycho_server_t* server, int32_t slot, int32_t* it
 int ptycho_server_release(ptycho_server_t* server, int32_t slot);
 /* Bytes currently counted against the budget. */
 int64_t ptycho_server_used_bytes(const ptycho_server_t* server);
+/* Selects the form of the tick (PTYCHO_SERVE_SHARED_LAUNCHES or PTYCHO_SERVE_SITE_GRAPHS);
+ * only while no site is admitted (PTYCHO_EINVAL otherwise, or for another mode). */
+int ptycho_server_set_mode(ptycho_server_t* server, int32_t mode);
 
 /* Opt-in per-kernel timing.  While enabled, every launch of a compute call is bracketed
  * by a CUDA event pair recorded on the call's stream.  ptycho_plan_profile_read waits for

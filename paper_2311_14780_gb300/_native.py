@@ -80,6 +80,7 @@ SIGNATURES = [
                                     c_int32_p, c_int32_p, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ptycho_plain_step", _I, [_VP, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP, _VP]),
     ("ptycho_server_create", _I, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_VP)]),
+    ("ptycho_server_set_mode", _I, [_VP, ctypes.c_int32]),
     ("ptycho_server_destroy", _I, [_VP]),
     ("ptycho_server_admit", _I, [_VP, ctypes.POINTER(Geom), ctypes.POINTER(Site), c_int32_p]),
     ("ptycho_server_tick", _I, [_VP, _VP, c_int32_p]),

@@ -112,15 +112,12 @@ __device__ __forceinline__ float sigma_of(const KArgs& a, int j) { return a.sigm
 // the row DFT (first half of f4).   grid (F/RPB, L, nb)
 // ---------------------------------------------------------------------------------------
 template <int F>
-__global__ void __launch_bounds__(RowCfg<F>::threads)
-k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void row_fwd_body(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, const KArgs& a, const uint3 bid) {
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowCfg<F>::T;
   extern __shared__ float2 smem[];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
-  const int r = blockIdx.x * RowCfg<F>::RPB + vec;
-  const int l = blockIdx.y, b = blockIdx.z;
+  const int r = bid.x * RowCfg<F>::RPB + vec;
+  const int l = bid.y, b = bid.z;
   const int mlo = max(a.chunk_base, l * a.M), mhi = min(a.chunk_base + a.chunk_len, (l + 1) * a.M);
   if (mlo >= mhi) return;                             // uniform over the block
   const int j = batch_pos(a, a.batch_off + b);
@@ -144,20 +141,25 @@ k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   }
 }
 
+template <int F>
+__global__ void __launch_bounds__(RowCfg<F>::threads)
+k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  row_fwd_body<F>(O, P, S, a, blockIdx);
+}
+
 // ---------------------------------------------------------------------------------------
 // forward column pass: column DFT (second half of f4), |Psi|^2 summed over a mode group
 // grid (F/W, G, nb)
 // ---------------------------------------------------------------------------------------
 template <int F, bool STORE>
-__global__ void __launch_bounds__(ColCfg<F>::threads)
-k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void col_fwd_body(float2* __restrict__ S, float* __restrict__ Ipart, const KArgs& a, int first_chunk, const uint3 bid) {
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % W, t = threadIdx.x / W;
-  const int col = blockIdx.x * W + c;
-  const int g = blockIdx.y, b = blockIdx.z;
+  const int col = bid.x * W + c;
+  const int g = bid.y, b = bid.z;
   const int m0 = g * a.MG, m1 = min(a.chunk_len, m0 + a.MG);
   float acc[N2];
 #pragma unroll
@@ -184,6 +186,14 @@ k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_
     if (!first_chunk) val += dst[rc * F + cc];
     dst[rc * F + cc] = val;
   }
+}
+
+template <int F, bool STORE>
+__global__ void __launch_bounds__(ColCfg<F>::threads)
+k_col_fwd(float2* __restrict__ S, float* __restrict__ Ipart, KArgs a, int first_chunk) {
+  pdl_wait();
+  pdl_trigger();
+  col_fwd_body<F, STORE>(S, Ipart, a, first_chunk, blockIdx);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -497,20 +507,17 @@ __device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
 // warp sums in FP64, in a fixed order, into one partial per (call entry, block).
 // grid (F*F/(kLossThreads*kLossPx), nb)
 template <int F>
-__global__ void __launch_bounds__(kLossThreads)
-k_loss(KArgs a, LossArgs la) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void loss_body(const KArgs& a, const LossArgs& la, const uint3 bid) {
   constexpr int FF = F * F, NB = loss_blocks<F>();
   __shared__ float red[6][kLossThreads / 32];
-  const int b = blockIdx.y;
+  const int b = bid.y;
   const int i = a.batch_off + b;
-  const int q0 = (blockIdx.x * kLossThreads + threadIdx.x) * kLossPx;
+  const int q0 = (bid.x * kLossThreads + threadIdx.x) * kLossPx;
   const int j = batch_pos(a, i);                     // uniform over the block
   if (j < 0) {
-    if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * NB + blockIdx.x] = 0.0;
-    if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * NB + blockIdx.x] = 0.0;
-    if (la.z_part && threadIdx.x == 0) la.z_part[(long long)i * NB + blockIdx.x] = 0.0;
+    if (la.loss_part && threadIdx.x == 0) la.loss_part[(long long)i * NB + bid.x] = 0.0;
+    if (la.sig_part && threadIdx.x == 0) la.sig_part[(long long)i * NB + bid.x] = 0.0;
+    if (la.z_part && threadIdx.x == 0) la.z_part[(long long)i * NB + bid.x] = 0.0;
     if (la.D)
 #pragma unroll
       for (int k = 0; k < kLossPx; k += 4)
@@ -594,8 +601,16 @@ k_loss(KArgs a, LossArgs la) {
     for (int wi = 0; wi < kLossThreads / 32; ++wi)
       sum += (double)red[2 * threadIdx.x][wi] + (double)red[2 * threadIdx.x + 1][wi];
     double* out = threadIdx.x == 0 ? la.loss_part : (threadIdx.x == 1 ? la.sig_part : la.z_part);
-    if (out) out[(long long)i * NB + blockIdx.x] = sum;
+    if (out) out[(long long)i * NB + bid.x] = sum;
   }
+}
+
+template <int F>
+__global__ void __launch_bounds__(kLossThreads)
+k_loss(KArgs a, LossArgs la) {
+  pdl_wait();
+  pdl_trigger();
+  loss_body<F>(a, la, blockIdx);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -615,13 +630,10 @@ struct AdjArgs {
 // read once and the positions' D loads are independent.   grid (F*F/256, ceil(nb/kRtPos))
 constexpr int kRtPos = 8;
 template <int F>
-__global__ void __launch_bounds__(256)
-k_remap_adj(KArgs a, AdjArgs aa) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void remap_adj_body(const KArgs& a, const AdjArgs& aa, const uint3 bid) {
   constexpr int FF = F * F;
-  const int u = blockIdx.x * 256 + threadIdx.x;
-  const int b0 = blockIdx.y * kRtPos;
+  const int u = bid.x * 256 + threadIdx.x;
+  const int b0 = bid.y * kRtPos;
   const int nbk = min(kRtPos, a.nb - b0);
   const int e0 = __ldg(aa.rt_ptr + u), e1 = __ldg(aa.rt_ptr + u + 1);
   const float* Db = aa.D + (long long)b0 * FF;
@@ -638,6 +650,14 @@ k_remap_adj(KArgs a, AdjArgs aa) {
 #pragma unroll
   for (int k = 0; k < kRtPos; ++k)
     if (k < nbk) aa.Gt[(long long)(b0 + k) * FF + u] = gv[k];
+}
+
+template <int F>
+__global__ void __launch_bounds__(256)
+k_remap_adj(KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
+  remap_adj_body<F>(a, aa, blockIdx);
 }
 
 // Background gradient, Eq. 1 (N is added before the remap): acc[u] += sum over the batch of
@@ -658,16 +678,13 @@ k_bg_accum(const float* __restrict__ G, int nb, float* __restrict__ acc) {
 // adjoint column pass: (2/F) G Psi, inverse column DFT.   grid (F/W, G, nb)
 // ---------------------------------------------------------------------------------------
 template <int F, bool STORE>
-__global__ void __launch_bounds__(ColCfg<F>::threads)
-k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void col_adj_body(float2* __restrict__ S, const KArgs& a, const AdjArgs& aa, const uint3 bid) {
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W;
   extern __shared__ float2 smem[];
   float* gt = reinterpret_cast<float*>(smem + W * Xch<F>::region_cols);   // [F][W]
   const int c = threadIdx.x % W, t = threadIdx.x / W;
-  const int col0 = blockIdx.x * W;
-  const int g = blockIdx.y, b = blockIdx.z;
+  const int col0 = bid.x * W;
+  const int g = bid.y, b = bid.z;
   const float* Gb = (aa.remap ? aa.Gt : aa.D) + (long long)b * F * F;
   const float scale = 2.0f / (float)F;
   for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
@@ -695,6 +712,14 @@ k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) base[(long long)(t + N1 * n2) * F] = v[n2];
   }
+}
+
+template <int F, bool STORE>
+__global__ void __launch_bounds__(ColCfg<F>::threads)
+k_col_adj(float2* __restrict__ S, KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
+  col_adj_body<F, STORE>(S, a, aa, blockIdx);
 }
 
 // Staged adjoint column pass (see k_col_fwd_s).   grid (F/W, nb), block W*T
@@ -834,19 +859,16 @@ template <int F> struct RowAdjCfg {
 };
 
 template <int F, bool ATOMIC>
-__global__ void __launch_bounds__(RowAdjCfg<F>::threads, (F <= 256 ? 2 : 1))
-k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
-          float2* __restrict__ gP, float2* __restrict__ gO, KArgs a) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void row_adj_body(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
+          float2* __restrict__ gP, float2* __restrict__ gO, const KArgs& a, const uint3 bid) {
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = RowAdjCfg<F>::T, RPB = RowAdjCfg<F>::RPB;
   extern __shared__ float2 smem[];
   __shared__ int2 spos[kMaxB];
   __shared__ float ssig[kMaxB];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
   const int slot = vec / RPB, rr = vec % RPB;
-  const int r = blockIdx.x * RPB + rr;
-  const int cm = blockIdx.y;
+  const int r = bid.x * RPB + rr;
+  const int cm = bid.y;
   const int mode = a.chunk_base + cm;
   const int l = mode / a.M;
   stage_batch(a, l, spos, ssig);
@@ -900,27 +922,33 @@ k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __
   }
 }
 
+template <int F, bool ATOMIC>
+__global__ void __launch_bounds__(RowAdjCfg<F>::threads, (F <= 256 ? 2 : 1))
+k_row_adj(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
+          float2* __restrict__ gP, float2* __restrict__ gO, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  row_adj_body<F, ATOMIC>(O, P, S, gP, gO, a, blockIdx);
+}
+
 // ---------------------------------------------------------------------------------------
 // object gradient: one block per 32x32 tile of grad O_l inside the batch's bounding box; it
 // adds, in a fixed order, every overlapping patch contribution of the chunk's modes.
 // grid (tiles of the largest box, L)
 // ---------------------------------------------------------------------------------------
 template <int F>
-__global__ void __launch_bounds__(256)
-k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void obj_grad_body(const float2* __restrict__ S, float2* __restrict__ gO, const KArgs& a, const uint3 bid) {
   __shared__ int2 spos[kMaxB];
   __shared__ float ssig[kMaxB];
-  const int l = blockIdx.y;
+  const int l = bid.y;
   const int mlo = max(a.chunk_base, l * a.M), mhi = min(a.chunk_base + a.chunk_len, (l + 1) * a.M);
   if (mlo >= mhi) return;                             // uniform over the block
   const int by0 = a.box[l][0], bx0 = a.box[l][1];
   const int ntx = (a.box[l][3] - bx0 + kTile - 1) / kTile;
   const int nty = (a.box[l][2] - by0 + kTile - 1) / kTile;
-  if ((int)blockIdx.x >= ntx * nty) return;          // uniform over the block
+  if ((int)bid.x >= ntx * nty) return;          // uniform over the block
   stage_batch(a, l, spos, ssig);
-  const int oy0 = by0 + ((int)blockIdx.x / ntx) * kTile, ox0 = bx0 + ((int)blockIdx.x % ntx) * kTile;
+  const int oy0 = by0 + ((int)bid.x / ntx) * kTile, ox0 = bx0 + ((int)bid.x % ntx) * kTile;
   const int H = a.obj_h[l], Wd = a.obj_w[l];
   const int tx = threadIdx.x % kTile, ty0 = threadIdx.x / kTile;   // 8 row slots
   const int ox = ox0 + tx;
@@ -957,6 +985,14 @@ k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
       *p = cadd(*p, acc[k]);
     }
   }
+}
+
+template <int F>
+__global__ void __launch_bounds__(256)
+k_obj_grad(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  obj_grad_body<F>(S, gO, a, blockIdx);
 }
 
 // ---------------------------------------------------------------------------------------

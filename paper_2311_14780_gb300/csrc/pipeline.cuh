@@ -5,6 +5,7 @@
 
 #include "plan.h"
 #include "resident.cuh"
+#include "serve_multi.cuh"
 
 namespace ptycho {
 

@@ -65,12 +65,16 @@ class Request:
 class Server:
     """``ptycho_server_t``: resident sites, budgeted admission, one graph launch per tick."""
 
-    def __init__(self, budget_bytes: int, max_sites: int = 128):
+    SHARED_LAUNCHES = 0
+    SITE_GRAPHS = 1
+
+    def __init__(self, budget_bytes: int, max_sites: int = 128, mode: int = 0):
         h = ctypes.c_void_p()
         _check(_native.lib().ptycho_server_create(int(budget_bytes), int(max_sites), ctypes.byref(h)),
                "ptycho_server_create")
         self._h = h
         self._keep = {}
+        _check(_native.lib().ptycho_server_set_mode(self._h, int(mode)), "ptycho_server_set_mode")
 
     def admit(self, r: Request) -> Optional[int]:
         """Slot of the admitted request, or None when it does not fit right now."""
@@ -128,8 +132,9 @@ class Server:
 
 
 def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, realtime: bool = True,
-                 max_tick_evals: Optional[int] = None) -> dict:
-    """Run the requests through a Server, admitting them as they arrive and fit.
+                 max_tick_evals: Optional[int] = None, mode: int = 0) -> dict:
+    """Run the requests through a Server (``mode``: Server.SHARED_LAUNCHES or SITE_GRAPHS),
+    admitting them as they arrive and fit.
 
     Requests are admitted in arrival order while the HBM budget allows and, if
     ``max_tick_evals`` is set, while the active sites' evaluations per tick stay within it
@@ -137,7 +142,7 @@ def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, r
     times are honoured against the wall clock; otherwise all requests are present at time
     0.  Returns the latency and throughput summary.
     """
-    sv = Server(budget_bytes, max_sites)
+    sv = Server(budget_bytes, max_sites, mode)
     stream = torch.cuda.current_stream()
     pending = sorted(reqs, key=lambda r: r.arrival_s)
     active = {}

@@ -46,12 +46,16 @@ def _request(F, L, M, n_side, seed, dev, iterations=4, name=None, arrival=0.0):
                    lr_O=1e-2, lr_P=1e-2)
 
 
+MODES = [0, 1]     # Server.SHARED_LAUNCHES (one launch per pass over all sites), Server.SITE_GRAPHS
+
+
 @pytest.mark.gpu
-def test_site_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("mode", MODES)
+def test_site_result_is_the_same_alone_and_in_the_mix(mode):
     from paper_2311_14780_gb300.serve import Server
     dev = torch.device("cuda", 0)
     a_alone = _request(64, 1, 2, 3, 40, dev, iterations=5)
-    sv = Server(8 << 30)
+    sv = Server(8 << 30, mode=mode)
     slot = sv.admit(a_alone)
     while sv.tick():
         pass
@@ -64,7 +68,7 @@ def test_site_result_is_the_same_alone_and_in_the_mix():
     a_mix = _request(64, 1, 2, 3, 40, dev, iterations=5)
     b = _request(128, 2, 1, 3, 41, dev, iterations=7)
     c = _request(64, 2, 3, 4, 42, dev, iterations=3)
-    sv = Server(8 << 30)
+    sv = Server(8 << 30, mode=mode)
     sb, sc = sv.admit(b), sv.admit(c)
     assert sv.tick() == 2
     sa = sv.admit(a_mix)
@@ -88,14 +92,16 @@ def test_site_result_is_the_same_alone_and_in_the_mix():
 
 
 @pytest.mark.gpu
-def test_served_iterations_match_ptycho_step():
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("F", [128, 512])
+def test_served_iterations_match_ptycho_step(mode, F):
     from paper_2311_14780_gb300 import AdamState
     from paper_2311_14780_gb300.api import plan_geometry_plan
     from paper_2311_14780_gb300.serve import Server
     dev = torch.device("cuda", 0)
-    r = _request(128, 2, 2, 3, 43, dev, iterations=3)
+    r = _request(F, 2, 2, 3, 43, dev, iterations=3)
     O0, P0 = r.O.clone(), r.P.clone()
-    sv = Server(8 << 30)
+    sv = Server(8 << 30, mode=mode)
     slot = sv.admit(r)
     while sv.tick():
         pass
@@ -162,13 +168,14 @@ def test_plain_step_matches_fused_step(F):
 
 
 @pytest.mark.gpu
-def test_reused_slot_runs_the_new_site():
+@pytest.mark.parametrize("mode", MODES)
+def test_reused_slot_runs_the_new_site(mode):
     """A released slot re-filled by another site, with the active slot set unchanged
-    ({0, 1} before and after): the tick must run the new site's graph."""
+    ({0, 1} before and after): the tick must run the new site's work."""
     from paper_2311_14780_gb300.serve import Server
     dev = torch.device("cuda", 0)
     b_alone = _request(128, 1, 2, 3, 48, dev, iterations=3)
-    sv = Server(8 << 30)
+    sv = Server(8 << 30, mode=mode)
     s = sv.admit(b_alone)
     while sv.tick():
         pass
@@ -179,7 +186,7 @@ def test_reused_slot_runs_the_new_site():
     a = _request(64, 1, 1, 3, 47, dev, iterations=2)
     c = _request(64, 2, 2, 3, 49, dev, iterations=6)
     b = _request(128, 1, 2, 3, 48, dev, iterations=3)
-    sv = Server(8 << 30)
+    sv = Server(8 << 30, mode=mode)
     sa, sc = sv.admit(a), sv.admit(c)
     assert (sa, sc) == (0, 1)
     assert sv.tick() == 2 and sv.tick() == 2     # a is done after two ticks
@@ -247,7 +254,8 @@ def _oracle_request(F, L, M, n_side, seed, dev, iterations):
 
 @pytest.mark.gpu
 @pytest.mark.slow
-def test_served_sites_follow_the_oracle():
+@pytest.mark.parametrize("mode", MODES)
+def test_served_sites_follow_the_oracle(mode):
     """The serving stream's rules in miniature: one site per frame size (128, 256, 512), with
     different wavelength and mode counts, admitted together and served in mixed ticks (one
     launch runs an iteration of every site).  After each of three iterations, every site's
@@ -267,7 +275,7 @@ def test_served_sites_follow_the_oracle():
     sites = [_oracle_request(128, 2, 2, 3, 61, dev, 3), _oracle_request(256, 1, 3, 2, 62, dev, 3),
              _oracle_request(512, 1, 2, 2, 63, dev, 3)]
     hp = dict(b1=float(np.float32(0.9)), b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)))
-    sv = Server(16 << 30)
+    sv = Server(16 << 30, mode=mode)
     slots = [sv.admit(s[0]) for s in sites]
     assert None not in slots
     ost = [orc.AdamState([tuple(sh) for sh in s[1].obj_shapes], tuple(s[0].P.shape)) for s in sites]
@@ -308,3 +316,47 @@ def test_served_sites_follow_the_oracle():
     for s in slots:
         sv.release(s)
     sv.close()
+
+
+@pytest.mark.gpu
+def test_shared_launches_cover_many_uneven_sites():
+    """Five sites of three frame sizes with uneven position counts (one, two and three position
+    batches per site, so later rounds carry fewer sites) and different wavelength and mode
+    counts: each site's result after three shared-launch ticks equals that of the same site
+    served alone, bit for bit, and ptycho_step's within the stated bar."""
+    from paper_2311_14780_gb300 import AdamState
+    from paper_2311_14780_gb300.api import plan_geometry_plan
+    from paper_2311_14780_gb300.serve import Server
+    dev = torch.device("cuda", 0)
+    specs = [(64, 2, 3, 6, 71), (128, 1, 4, 9, 72), (64, 1, 1, 3, 73), (256, 2, 2, 5, 74), (128, 3, 2, 4, 75)]
+    mixed = [_request(F, L, M, n, seed, dev, iterations=3) for (F, L, M, n, seed) in specs]
+    start = [(r.O.clone(), r.P.clone()) for r in mixed]
+    sv = Server(16 << 30)
+    slots = [sv.admit(r) for r in mixed]
+    assert None not in slots
+    while sv.tick():
+        pass
+    torch.cuda.synchronize()
+    losses = [sv.status(k)[1] for k in slots]
+    for k in slots:
+        sv.release(k)
+    sv.close()
+    for spec, r, (O0, P0), loss in zip(specs, mixed, start, losses):
+        alone = _request(*spec[:4], spec[4], dev, iterations=3)
+        sv = Server(16 << 30)
+        k = sv.admit(alone)
+        while sv.tick():
+            pass
+        torch.cuda.synchronize()
+        assert sv.status(k)[1] == loss, spec
+        sv.release(k)
+        sv.close()
+        assert torch.equal(alone.O, r.O) and torch.equal(alone.P, r.P), spec
+        plan = plan_geometry_plan(r)
+        st = AdamState(plan, r.lr_O, r.lr_P)
+        for _ in range(3):
+            plan.step(st, O0, P0, r.I_meas)
+        torch.cuda.synchronize()
+        assert rel(r.O.cpu().numpy(), O0.cpu().numpy()) < 1e-4, spec
+        assert rel(r.P.cpu().numpy(), P0.cpu().numpy()) < 1e-4, spec
+        plan.close()
