@@ -76,9 +76,11 @@ extern "C" {
  *   (cp.async, double-buffered) while the current one is transformed (one intensity slice, no
  *   mode groups).  Measured slower than the default mode groups on every benchmark workload
  *   (fewer warps per SM); NARROW_COLUMNS takes 4 columns per block instead of 8.
- * FUSED_ROW_FWD: the forward row pass over all modes of a wavelength per block, the probe row
- *   in registers and the next position's object rows prefetched (cp.async).  Measured slower
- *   than the default one-position-per-block pass.
+ * FUSED_ROW_FWD / UNFUSED_ROW_FWD: the forward row pass over all modes of a wavelength per
+ *   block, the probe row in registers and the next position's object rows prefetched
+ *   (cp.async) / one block per position and row block.  Default: fused at F = 512 from 4 modes
+ *   (the probes outgrow the L2 there; measured 2-3 % faster), per position otherwise (measured
+ *   faster with one mode and at 256^2).  UNFUSED_ROW_FWD wins when both are given.
  * NO_PDL: launch without programmatic dependent launch.
  * ROW_ADJ_PROBE_L2 / ROW_ADJ_PROBE_SMEM: the fused row adjoint reads its probe rows through
  *   L1/L2 (and is compiled for two blocks of at most 160 threads per SM) / holds them in shared
@@ -105,6 +107,7 @@ extern "C" {
 #define PTYCHO_FLAG_RESIDENT_FRAMES 1024
 #define PTYCHO_FLAG_ROW_ADJ_PROBE_L2 2048
 #define PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM 4096
+#define PTYCHO_FLAG_UNFUSED_ROW_FWD 8192
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */

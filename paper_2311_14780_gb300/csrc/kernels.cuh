@@ -109,7 +109,7 @@ __device__ __forceinline__ float sigma_of(const KArgs& a, int j) { return a.sigm
 
 // ---------------------------------------------------------------------------------------
 // forward row pass: exit waves (f1, f2, f3) of every mode of wavelength l in the chunk and
-// the row DFT (first half of f4).   grid (F/RPB, L, nb)
+// the row DFT (first half of f4).   block index (row block, l, position b)
 // ---------------------------------------------------------------------------------------
 template <int F>
 __device__ __forceinline__ void row_fwd_body(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, const KArgs& a, const uint3 bid) {
@@ -141,12 +141,15 @@ __device__ __forceinline__ void row_fwd_body(const float2* __restrict__ O, const
   }
 }
 
+// grid (nb, F/RPB, L): the positions of a batch vary fastest, so that the blocks running at the
+// same time share probe rows in L2 (the probes of all modes can exceed the L2: 120 MB at 512^2
+// with 6 wavelengths x 10 modes)
 template <int F>
 __global__ void __launch_bounds__(RowCfg<F>::threads)
 k_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a) {
   pdl_wait();
   pdl_trigger();
-  row_fwd_body<F>(O, P, S, a, blockIdx);
+  row_fwd_body<F>(O, P, S, a, make_uint3(blockIdx.y, blockIdx.z, blockIdx.x));
 }
 
 // ---------------------------------------------------------------------------------------

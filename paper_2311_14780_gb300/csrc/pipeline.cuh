@@ -290,7 +290,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
                               row_fwd_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, a, p.rpb_adj, p.nsplit_fwd));
       else
         PTY_LAUNCH(p, kRowFwd, cs,
-                   launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
+                   launch_pdl(k_row_fwd<F>, dim3(a.nb, F / RowCfg<F>::RPB, p.L), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
       const dim3 col_grid(F / ColCfg<F>::W, p.G, a.nb);
       if (col_staged) {
         rc = narrow ? launch_cols_s<F, 4>(p, true, store, cs, S, Ip, a, aa) : launch_cols_s<F, 0>(p, true, store, cs, S, Ip, a, aa);
@@ -351,7 +351,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       }
       if (!store && rerun_rows)
         PTY_LAUNCH(p, kRowFwd, cs,
-                   launch_pdl(k_row_fwd<F>, dim3(F / RowCfg<F>::RPB, p.L, a.nb), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
+                   launch_pdl(k_row_fwd<F>, dim3(a.nb, F / RowCfg<F>::RPB, p.L), row_blk, RowCfg<F>::smem, cs, c.O, c.P, S, a));
       if (col_staged) {
         rc = narrow ? launch_cols_s<F, 4>(p, false, store, cs, S, Ip, a, aa) : launch_cols_s<F, 0>(p, false, store, cs, S, Ip, a, aa);
         if (rc) return rc;

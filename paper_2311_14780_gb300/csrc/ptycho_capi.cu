@@ -584,8 +584,13 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
         ns = std::min<long long>(ns, std::min<long long>(64, p->B));
         while (ns > 1 && ns * p->P_numel * (long long)sizeof(float2) > (512ll << 20)) --ns;
         p->nsplit_adj = (int)std::max<long long>(1, ns);
-        // the forward row pass: same blocks, positions split for four blocks per SM
-        if (g->flags & PTYCHO_FLAG_FUSED_ROW_FWD) {
+        // the forward row pass: same blocks, positions split for four blocks per SM.  Default at
+        // 512^2 from 4 modes, where the probes of all modes outgrow the L2 and the fused pass reads
+        // each probe row once per block instead of once per position: measured 153.4 vs 157.2 ms
+        // on config 4, 45.9 vs 47.4 ms on 8 modes x 5 wavelengths, 15.8 vs 16.4 on 4 x 3; slower
+        // with one mode (3.62 vs 3.37 ms) and at 256^2 (3.32 vs 3.27 ms on config 2)
+        const bool fwd_default = F == 512 && g->M >= 4 && !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_FWD);
+        if (((g->flags & PTYCHO_FLAG_FUSED_ROW_FWD) && !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_FWD)) || fwd_default) {
           p->fwd_l = 1;
           p->nsplit_fwd = (int)std::max<long long>(1, std::min<long long>((4ll * p->sms + base - 1) / base, p->B));
         }

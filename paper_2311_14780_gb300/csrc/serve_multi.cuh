@@ -73,7 +73,8 @@ template <int F>
 __global__ void __launch_bounds__(RowCfg<F>::threads) k_row_fwd_multi(RoundTab rt) {
   __shared__ SiteRound w;
   const int loc = load_site(rt, kMpRowFwd, w);
-  row_fwd_body<F>(w.O, w.P, w.S, w.a, unflatten(loc, F / RowCfg<F>::RPB, w.a.L));
+  const uint3 u = unflatten(loc, w.a.nb, F / RowCfg<F>::RPB);      // positions fastest (probe rows shared in L2)
+  row_fwd_body<F>(w.O, w.P, w.S, w.a, make_uint3(u.y, u.z, u.x));
 }
 
 template <int F, bool STORE>

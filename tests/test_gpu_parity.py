@@ -144,12 +144,13 @@ def strong_z(F):
     return F * 15e-6 / 0.5
 
 
-@pytest.mark.parametrize("flags", [0, 32, 4096])
+@pytest.mark.parametrize("flags", [0, 32, 4096, 8192])
 def test_fused_row_adjoint_at_512_with_eight_modes(dev, flags):
-    """F = 512 with 8 modes takes the fused row adjoint (all modes of a wavelength per block,
-    object-gradient rows summed over the modes in shared memory; probe rows through L1/L2);
-    flag 32 forces the per-mode kernel, flag 4096 the variant that holds the probe rows in
-    shared memory.  Several position batches and splits."""
+    """F = 512 with 8 modes takes the fused row passes (all modes of a wavelength per block:
+    forward rows with the probe row in registers; adjoint rows with the object-gradient rows
+    summed over the modes in shared memory and the probe rows through L1/L2); flag 32 forces the
+    per-mode row adjoint, 4096 the row adjoint that holds the probe rows in shared memory, 8192
+    the per-position forward row pass.  Several position batches and splits."""
     w = syn.tiny_workload(F=512, L=1, M=8, n_side=3, step=64, seed=77, remap=True, loss="poisson",
                           with_sigma=True, with_bg=True)
     case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=12)
