@@ -132,7 +132,8 @@ template <int F> struct CztRowAdjCfg {
   static constexpr int smem = smem_xch > smem_red ? smem_xch : smem_red;
 };
 
-// exit waves and the row transform.   grid (F/RPB, L, nb)
+// exit waves and the row transform.   grid (nb, F/RPB, L): positions vary fastest, so that the
+// blocks running at the same time share probe rows in L2
 template <int F>
 __global__ void __launch_bounds__(CztRowCfg<F>::threads)
 k_czt_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a,
@@ -142,8 +143,8 @@ k_czt_row_fwd(const float2* __restrict__ O, const float2* __restrict__ P, float2
   constexpr int N1 = CztShape<F>::N1, NF = CztShape<F>::NF, T = CztRowCfg<F>::T;
   extern __shared__ float2 smem[];
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
-  const int r = blockIdx.x * CztRowCfg<F>::RPB + vec;
-  const int l = blockIdx.y, b = blockIdx.z;
+  const int r = blockIdx.y * CztRowCfg<F>::RPB + vec;
+  const int l = blockIdx.z, b = blockIdx.x;
   const int mlo = max(a.chunk_base, l * a.M), mhi = min(a.chunk_base + a.chunk_len, (l + 1) * a.M);
   if (mlo >= mhi) return;                             // uniform over the block
   const int j = batch_pos(a, a.batch_off + b);

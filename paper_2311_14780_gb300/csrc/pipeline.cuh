@@ -276,7 +276,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       a.chunk_len = (LM - a.chunk_base < p.C) ? (LM - a.chunk_base) : p.C;
       {
         if (p.czt) {                                  // chirp-z propagator
-          PTY_LAUNCH(p, kRowFwd, cs, launch_pdl(k_czt_row_fwd<F>, dim3(F / CztRowCfg<F>::RPB, p.L, a.nb),
+          PTY_LAUNCH(p, kRowFwd, cs, launch_pdl(k_czt_row_fwd<F>, dim3(a.nb, F / CztRowCfg<F>::RPB, p.L),
                                                 CztRowCfg<F>::threads, CztRowCfg<F>::smem, cs, c.O, c.P, S, a, ct));
           PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_czt_col_fwd<F>, dim3(F / CztColCfg<F>::W, p.G, a.nb),
                                                 CztColCfg<F>::threads, CztColCfg<F>::smem_fwd, cs, (const float2*)S, Ip,

@@ -200,9 +200,15 @@ void fill_round(Site* s, int r, ptycho::SiteRound& w, int& tiles, int* counts) {
   w.Ipart = p.d_Ipart;
   w.gO = p.d_gO;
   w.gP = p.d_gP;
-  const int rows = 256 / T;                          // RowCfg RPB = ColCfg W
+  int rows = 0, cols = 0;                           // RowCfg<F>::RPB, ColCfg<F>::W
+  switch (F) {
+    case 64: rows = RowCfg<64>::RPB; cols = ColCfg<64>::W; break;
+    case 128: rows = RowCfg<128>::RPB; cols = ColCfg<128>::W; break;
+    case 256: rows = RowCfg<256>::RPB; cols = ColCfg<256>::W; break;
+    default: rows = RowCfg<512>::RPB; cols = ColCfg<512>::W; break;
+  }
   counts[kMpRowFwd] = (F / rows) * p.L * a.nb;
-  counts[kMpColFwd] = (F / rows) * p.G * a.nb;
+  counts[kMpColFwd] = (F / cols) * p.G * a.nb;
   counts[kMpLoss] = (F * F / (kLossThreads * kLossPx)) * a.nb;
   counts[kMpRemapAdj] = p.remap ? (F * F / 256) * ((a.nb + kRtPos - 1) / kRtPos) : 0;
   counts[kMpColAdj] = counts[kMpColFwd];
