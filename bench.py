@@ -604,8 +604,9 @@ def run_ours(args, rank: int, world: int):
                "h2d_bytes_per_step": int(Ih_pinned.numel() * 4), "d2h_bytes_per_step": 8,
                "steps": e_steps, "ms_per_step": e_ms / e_steps,
                "note": "ptycho_step_host (C ABI): I_meas in pinned host memory copied to the device with "
-                       "cudaMemcpyAsync on the stream, the step, and the FP64 loss copied back to pinned host "
-                       "memory, every step; CUDA events around all of it"}
+                       "cudaMemcpyAsync every step (batch by batch on a side stream that starts after the previous "
+                       "step, each batch's loss waiting for its own frames), the step, and the FP64 loss copied back "
+                       "to pinned host memory; CUDA events on the caller's stream around all of it"}
         del Ih_pinned
 
     corrections = None

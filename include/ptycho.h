@@ -322,7 +322,10 @@ int ptycho_step(ptycho_plan_t* plan, ptycho_adam_t* state, float* O, float* P, f
  * "Discussion"; this entry point is the form for data that stay on the host).  On stream:
  * I_meas_host (HOST, J*F*F floats, camera grid; page-locked memory makes the copy
  * asynchronous, pageable memory makes this call wait for it) is copied into the caller's
- * DEVICE buffer I_meas_dev (J*F*F floats), ptycho_step runs on it with the other arguments
+ * DEVICE buffer I_meas_dev (J*F*F floats; over all positions in order, batch by batch on a
+ * plan-owned side stream that starts after the work already queued on stream, each position
+ * batch's loss waiting only for its own frames, so the copies overlap the transforms of earlier
+ * batches), ptycho_step runs on it with the other arguments
  * as documented there (loss_dev: DEVICE, 1 double, required here), and the loss is copied
  * into loss_host (HOST, 1 double), valid once the stream has passed this point.  The library
  * allocates nothing here.  PTYCHO_EINVAL for a NULL plan, I_meas_host, I_meas_dev, loss_dev

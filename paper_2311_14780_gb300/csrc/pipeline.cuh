@@ -308,6 +308,7 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, false>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
                                               (int)(ch == 0)));
     }
+    if (p.imeas_ready && cudaStreamWaitEvent(cs, p.imeas_ready[k], 0) != cudaSuccess) return PTYCHO_ECUDA;
     PTY_LAUNCH(p, kLoss, cs, launch_pdl(k_loss<F>, dim3(loss_blocks<F>(), a.nb), kLossThreads, 0, cs, a, la));
     if (!grad) continue;
     if (p.remap) PTY_LAUNCH(p, kRemapAdj, cs, launch_pdl(k_remap_adj<F>, dim3(FF / 256, (a.nb + kRtPos - 1) / kRtPos), 256, 0, cs, a, aa));

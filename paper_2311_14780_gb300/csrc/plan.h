@@ -109,6 +109,13 @@ struct ptycho_plan {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<int> ev_kind;                    // kind of the launch of each event pair
+
+  // ptycho_step_host: the measured patterns are copied batch by batch on copy_st; the loss kernel
+  // of position batch k waits for ev_copy[k] (set only for the duration of that call)
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_copy_start = nullptr;
+  std::vector<cudaEvent_t> ev_copy;
+  const cudaEvent_t* imeas_ready = nullptr;
 };
 
 namespace ptycho {

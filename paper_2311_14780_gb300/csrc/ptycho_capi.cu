@@ -277,6 +277,9 @@ int load_czt(ptycho_plan* p, const double* zoom) {
 
 void free_plan(ptycho_plan* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_copy) cudaEventDestroy(e);
+  if (p->ev_copy_start) cudaEventDestroy(p->ev_copy_start);
+  if (p->copy_st) cudaStreamDestroy(p->copy_st);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   for (int i = 0; i < ptycho_plan::kMaxSets; ++i) {
     if (p->ev_radj[i]) cudaEventDestroy(p->ev_radj[i]);
@@ -1009,12 +1012,46 @@ int ptycho_step_host(ptycho_plan_t* p, ptycho_adam_t* s, float* O, float* P, flo
   int rc = check_device(p);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t bytes = sizeof(float) * (size_t)p->J * (size_t)p->F * (size_t)p->F;
-  if (cudaMemcpyAsync(I_meas_dev, I_meas_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-    cudaGetLastError();
-    return PTYCHO_ECUDA;
+  const size_t frame = sizeof(float) * (size_t)p->F * (size_t)p->F;
+  const int nbat = (p->J + p->B - 1) / p->B;
+  if (batch_idx || !p->store || p->nchunks != 1) {
+    // positions in any order (or one position at a time): one copy before the step
+    if (cudaMemcpyAsync(I_meas_dev, I_meas_host, frame * (size_t)p->J, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      return PTYCHO_ECUDA;
+    }
+    rc = ptycho_step(p, s, O, P, sigma, bg, I_meas_dev, mask, mask_per_frame, batch_idx, nbatch, loss_dev, stream);
+  } else {
+    // all positions in order: batch k's frames are copied on a side stream after the work queued
+    // on stream so far, and its loss kernel waits only for them, so the copies of later batches
+    // overlap the transforms of earlier ones
+    if (!p->copy_st && (cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&p->ev_copy_start, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      return PTYCHO_ECUDA;
+    }
+    while ((int)p->ev_copy.size() < nbat) {
+      cudaEvent_t e;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PTYCHO_ECUDA;
+      p->ev_copy.push_back(e);
+    }
+    if (cudaEventRecord(p->ev_copy_start, st) != cudaSuccess ||
+        cudaStreamWaitEvent(p->copy_st, p->ev_copy_start, 0) != cudaSuccess)
+      return PTYCHO_ECUDA;
+    for (int k = 0; k < nbat; ++k) {
+      const size_t off = (size_t)k * p->B, n = (size_t)std::min(p->B, p->J - k * p->B);
+      if (cudaMemcpyAsync(reinterpret_cast<char*>(I_meas_dev) + off * frame,
+                          reinterpret_cast<const char*>(I_meas_host) + off * frame, n * frame,
+                          cudaMemcpyHostToDevice, p->copy_st) != cudaSuccess ||
+          cudaEventRecord(p->ev_copy[k], p->copy_st) != cudaSuccess) {
+        cudaGetLastError();
+        return PTYCHO_ECUDA;
+      }
+    }
+    p->imeas_ready = p->ev_copy.data();
+    rc = ptycho_step(p, s, O, P, sigma, bg, I_meas_dev, mask, mask_per_frame, batch_idx, nbatch, loss_dev, stream);
+    p->imeas_ready = nullptr;
   }
-  rc = ptycho_step(p, s, O, P, sigma, bg, I_meas_dev, mask, mask_per_frame, batch_idx, nbatch, loss_dev, stream);
   if (rc) return rc;
   if (cudaMemcpyAsync(loss_host, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
     cudaGetLastError();
