@@ -94,6 +94,12 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
+  if constexpr (F >= 512) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_2b<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_2b<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<F>::smem_xch);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_2b<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_2b<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_adj_smem);
+  }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_fwd);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_fwd);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma<F>::smem_adj);
@@ -301,6 +307,12 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       else if (p.has_tma)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, false>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
                                               p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
+      else if (F >= 512 && store)
+        PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_2b<F, true>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip,
+                                              a, (int)(ch == 0)));
+      else if (F >= 512)
+        PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_2b<F, false>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip,
+                                              a, (int)(ch == 0)));
       else if (store)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd<F, true>, col_grid, col_blk, ColCfg<F>::smem_xch, cs, S, Ip, a,
                                               (int)(ch == 0)));
@@ -362,6 +374,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       else if (p.has_tma)
         PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_tma<F, false>, col_grid, col_blk, ColTma<F>::smem_adj, cs,
                                               p.tmap_S[set], S, a, aa));
+      else if (F >= 512 && store)
+        PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_2b<F, true>, col_grid, col_blk, col_adj_smem, cs, S, a, aa));
+      else if (F >= 512)
+        PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_2b<F, false>, col_grid, col_blk, col_adj_smem, cs, S, a, aa));
       else if (store)
         PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj<F, true>, col_grid, col_blk, col_adj_smem, cs, S, a, aa));
       else

@@ -682,10 +682,11 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
       default: W = ptycho::ColCfg<512>::W; break;
     }
     const long long rows = (long long)p->B * p->C * F;
-    // measured: the staged column passes pay off from F = 512 up, and at F = 128 once a position
-    // has four or more fields (3-6 % on 128^2 with L*M = 5..40; 2 % slower with L*M = 1; at
-    // F = 256 and F = 64 they measured slower or equal)
-    const bool tma_default = F >= 512 || (F == 128 && p->C >= 4);
+    // measured: the staged column passes pay off at F = 512 from two fields per position up (one
+    // field: the plain-load passes, two blocks per SM, are 10 % faster), and at F = 128 once a
+    // position has four or more fields (3-6 % on 128^2 with L*M = 5..40; 2 % slower with L*M = 1;
+    // at F = 256 and F = 64 they measured slower or equal)
+    const bool tma_default = (F >= 512 && p->C >= 2) || (F == 128 && p->C >= 4);
     p->has_tma = (g->flags & PTYCHO_FLAG_NO_TMA) || p->czt ? 0 : ((g->flags & PTYCHO_FLAG_TMA) || tma_default) ? 1 : 0;
     for (int i = 0; i < p->nsets; ++i)
       if (p->has_tma && !make_column_map(&p->tmap_S[i], p->d_S + (long long)i * p->B * p->C * FF, F, rows, W))
