@@ -82,10 +82,19 @@ extern "C" {
  *   (the probes outgrow the L2 there; measured 2-3 % faster), per position otherwise (measured
  *   faster with one mode and at 256^2).  UNFUSED_ROW_FWD wins when both are given.
  * NO_PDL: launch without programmatic dependent launch.
- * ROW_ADJ_PROBE_L2 / ROW_ADJ_PROBE_SMEM: the fused row adjoint reads its probe rows through
- *   L1/L2 (and is compiled for two blocks of at most 160 threads per SM) / holds them in shared
- *   memory for the batch.  Default: L1/L2 at F = 512 when T*M*rpb <= 160 (measured 1-3 % faster
- *   there), shared memory otherwise.  PROBE_SMEM wins when both are given.
+ * ROWS_16_THREADS: at F = 512 the fused row adjoint takes one warp per row (16 values per lane,
+ *   probe rows through L1/L2, two blocks of at most 320 threads per SM) whenever 32*M*rpb <= 320:
+ *   measured 6 % faster on 512^2 x 10 modes x 6 wavelengths than 16 threads per row.  This flag
+ *   keeps 16 threads per row in both fused row passes (so do ROW_ADJ_PROBE_L2 and
+ *   ROW_ADJ_PROBE_SMEM for the adjoint).
+ * FWD_ROWS_WARP: at F = 512 the fused forward row pass with one warp per row as well (when
+ *   32*M*rpb <= 320).  Measured 1.7 % slower per step on 512^2 x 10 modes x 6 wavelengths (146.4
+ *   vs 144.0 ms): its twice as many resident warps take the SMs from the other streams' passes.
+ * ROW_ADJ_PROBE_L2 / ROW_ADJ_PROBE_SMEM: the fused row adjoint with T threads per row reads its
+ *   probe rows through L1/L2 (and is compiled for two blocks of at most 160 threads per SM) /
+ *   holds them in shared memory for the batch.  Default below F = 512: shared memory; at F = 512
+ *   where the one-warp rows do not fit, L1/L2 when T*M*rpb <= 160.  PROBE_SMEM wins when both are
+ *   given.
  * RESIDENT_FRAMES: at F <= 128, frame-resident passes instead of the scratch passes: one
  *   block holds a whole F x F field in shared memory, so exit waves and spectra never leave
  *   the SM; the forward writes only the per-position intensity, the adjoint recomputes Psi on
@@ -108,6 +117,8 @@ extern "C" {
 #define PTYCHO_FLAG_ROW_ADJ_PROBE_L2 2048
 #define PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM 4096
 #define PTYCHO_FLAG_UNFUSED_ROW_FWD 8192
+#define PTYCHO_FLAG_ROWS_16_THREADS 16384
+#define PTYCHO_FLAG_FWD_ROWS_WARP 32768
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */

@@ -220,6 +220,89 @@ __device__ __forceinline__ void fft_inv_O2I(float2 (&x)[FftShape<F>::N2], int t,
   Dft<N2, 1, true>::run(x);
 }
 
+// Inverse (unscaled, the adjoint of the forward DFT) 512-point transform by a whole warp, 16 values
+// per lane, for kernels that hold a spectrum row in shared memory in natural order.  With
+// n = t + 32 n2 and k = c + 16 k1 (t, lane in [0, 32); c, n2 in [0, 16); k1 in [0, 32)):
+//   x[t + 32 n2] = sum_c W16^(-n2 c) W512^(-t c) sum_k1 X[c + 16 k1] W32^(-t k1).
+// The inner 32-point sum is split by the parity q of k1 = 2 s + q: lane u = c + 16 q takes the 16
+// spectrum values X[u + 32 s] (a 16-point inverse DFT over s), lanes with q = 1 apply W32^(-j),
+// and the pair (u, u ^ 16) combines E + T and E - T through a shuffle, giving Y[c][t] for
+// t = j + 16 q.  Each element is multiplied by W512^(-t c) (the F = 512 table entry tw[t*16 + c]),
+// the 16 x 32 block is transposed through ``xc`` (element (c, t) at c*33 + t: conflict-free in
+// both directions), and lane t takes a 16-point inverse DFT over c.  ``spec`` may alias ``xc`` (the spectrum is
+// read before the first write).  Out: x[n2] = value at n = lane + 32 n2 (layout I of 32 lanes).
+__device__ __forceinline__ void fft512_inv_warp(const float2* spec, float2 (&x)[16], int lane, float2* xc,
+                                                const float2* __restrict__ tw) {
+  constexpr int R = 33;
+  const int c = lane & 15, q = lane >> 4;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) x[s] = spec[lane + 32 * s];
+  __syncwarp();                                       // spec may be xc
+  Dft<16, 1, true>::run(x);
+  if (q) {
+    static_for<1, 16>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      x[j] = twiddle_const<32, true, j>(x[j]);
+    });
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float ox = __shfl_xor_sync(0xffffffffu, x[j].x, 16), oy = __shfl_xor_sync(0xffffffffu, x[j].y, 16);
+    x[j] = q ? make_float2(ox - x[j].x, oy - x[j].y) : make_float2(x[j].x + ox, x[j].y + oy);
+  }
+  // W512^(-t c) before the transpose: lane (c, q) reads tw[t*16 + c], t = j + 16 q, two
+  // contiguous 128-byte runs per warp load (after the transpose the same factors would be a
+  // 128-byte stride across the lanes)
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j > 0 || q) x[j] = cmulc(x[j], __ldg(tw + (j + 16 * q) * 16 + c));
+    xc[c * R + j + 16 * q] = x[j];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = xc[k * R + lane];
+  __syncwarp();                                       // the region may be reused right away
+  Dft<16, 1, true>::run(x);
+}
+constexpr int kFft512WarpXch = 16 * 33;               // exchange elements of fft512_inv_warp
+
+// Forward 512-point transform by a whole warp, the mirror of fft512_inv_warp.  In: x[n2] = value
+// at n = lane + 32 n2.  With k = c + 16 k1 and n = t + 32 n2:
+//   X[c + 16 k1] = sum_t W32^(t k1) W512^(t c) sum_n2 x[t + 32 n2] W16^(n2 c).
+// Lane t takes the 16-point DFT over n2 (A[t][c]); A is transposed through ``xc`` (element
+// (t, c) at t*17 + c); lane (c, q), q = lane >> 4, takes A[2 s + q][c] W512^((2 s + q) c) for
+// s in [0, 16) (table entry tw[(2 s + q)*16 + c], contiguous over the warp), a 16-point DFT over
+// s, W32^j on the q = 1 lanes and the butterfly with lane ^ 16.  Out: lane (c, q) holds
+// X[c + 16 j + 256 q] in x[j] (for each j the warp covers two contiguous 16-element runs).
+__device__ __forceinline__ void fft512_fwd_warp(float2 (&x)[16], int lane, float2* xc, const float2* __restrict__ tw) {
+  constexpr int R = 17;
+  const int c = lane & 15, q = lane >> 4;
+  Dft<16, 1, false>::run(x);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) xc[lane * R + k] = x[k];
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int t = 2 * s + q;
+    x[s] = xc[t * R + c];
+    if (s > 0 || q) x[s] = cmul(x[s], __ldg(tw + t * 16 + c));
+  }
+  __syncwarp();                                       // the region may be reused right away
+  Dft<16, 1, false>::run(x);
+  if (q) {
+    static_for<1, 16>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      x[j] = twiddle_const<32, false, j>(x[j]);
+    });
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float ox = __shfl_xor_sync(0xffffffffu, x[j].x, 16), oy = __shfl_xor_sync(0xffffffffu, x[j].y, 16);
+    x[j] = q ? make_float2(ox - x[j].x, oy - x[j].y) : make_float2(x[j].x + ox, x[j].y + oy);
+  }
+}
+constexpr int kFft512WarpXchF = 32 * 17;              // exchange elements of fft512_fwd_warp
+
 // Index helpers for the two layouts.
 template <int F> __device__ __forceinline__ int idxI(int t, int n2) { return t + FftShape<F>::N1 * n2; }
 template <int F> __device__ __forceinline__ int idxO(int t, int slot) {

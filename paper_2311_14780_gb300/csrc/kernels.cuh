@@ -1151,6 +1151,94 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
   }
 }
 
+// Same pass at F = 512 with one warp per row (fft512_inv_warp: 16 values per lane instead of 32
+// per thread of a 16-thread vector), probe rows through L1/L2: the row and its probe-gradient
+// sums take half the registers, so twice as many warps fit on an SM.  Vector v (warp v) takes
+// row blockIdx.x*rpb + v/M of mode v%M; element n of the row is value n/32 of lane n%32.
+// grid (512/rpb, L, nsplit), block 32*M*rpb <= kRowAdjWThreads, dynamic smem row_adj_w_smem(M, rpb)
+constexpr int kRowAdjWThreads = 320;
+constexpr int kRowAdjWRegion = kFft512WarpXch;      // per-vector row / exchange / mode-sum area (>= 512)
+__host__ __device__ constexpr int row_adj_w_smem(int M, int rpb) {
+  return (2 * M * rpb * kRowAdjWRegion + 2 * rpb * 512) * (int)sizeof(float2);
+}
+
+template <int F>
+__global__ void __launch_bounds__(kRowAdjWThreads, 2)
+k_row_adj_w(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
+            float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
+  static_assert(F == 512, "one warp per row is the 512-point layout");
+  pdl_wait();
+  pdl_trigger();
+  constexpr int RR = kRowAdjWRegion;
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
+  const int M = a.M, V = M * rpb;
+  float2* Sst = smem;                                 // [2][V][RR] scratch rows / exchange / mode sums
+  float2* Ost = Sst + 2 * V * RR;                     // [2][rpb][F] object rows
+  const int vec = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int rr = vec / M, m = vec % M;
+  const int row0 = blockIdx.x * rpb, r = row0 + rr;
+  const int l = blockIdx.y, split = blockIdx.z;
+  const int cm = l * M + m - a.chunk_base;
+  const int slot0 = l * M - a.chunk_base;
+  stage_batch(a, l, spos, ssig);
+  const float2* Prow = P + ((long long)(l * M + m) * F + r) * F;
+  const float2* Ol = O + a.obj_off[l];
+  const int Wl = a.obj_w[l];
+  auto prefetch = [&](int b, int buf) {
+    const float2* row = S + (((long long)b * a.C + cm) * F + r) * F;
+    float2* dst = Sst + (buf * V + vec) * RR;
+#pragma unroll
+    for (int k = 0; k < F / 64; ++k) cp_async16(dst + 2 * (t + 32 * k), row + 2 * (t + 32 * k));
+    if (a.patch)
+      prefetch_orows<F>(a.patch + ((long long)b * a.L + l) * F * F, F, make_int2(0, 0), row0, rpb, Ost + buf * rpb * F);
+    else
+      prefetch_orows<F>(Ol, Wl, spos[b], row0, rpb, Ost + buf * rpb * F);
+    cp_async_commit();
+  };
+  float2 acc[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) acc[n2] = make_float2(0.f, 0.f);
+  int b = next_pos(spos, split - nsplit, a.nb, nsplit);
+  if (b >= 0) prefetch(b, 0);
+  for (int buf = 0; b >= 0; buf ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();                                  // position b has landed; buffer buf^1 is free
+    const int bn = next_pos(spos, b, a.nb, nsplit);
+    if (bn >= 0) prefetch(bn, buf ^ 1);
+    const float s = ssig[b];
+    float2* reg = Sst + (buf * V + vec) * RR;
+    const float2* orow = Ost + (buf * rpb + rr) * F;
+    float2 v[16];
+    fft512_inv_warp(reg, v, t, reg, a.tw);
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) {
+      const int c = t + 32 * n2;
+      const float2 gp = cconjmul(orow[c], v[n2]);                       // conj(p) chi
+      acc[n2].x = fmaf(s, gp.x, acc[n2].x);
+      acc[n2].y = fmaf(s, gp.y, acc[n2].y);
+      reg[c] = cscale(cconjmul(__ldg(Prow + c), v[n2]), s);             // conj(sigma P) chi
+    }
+    __syncthreads();
+    float2* dst = S + (((long long)b * a.C + slot0) * F + row0) * F;
+    for (int e = threadIdx.x; e < rpb * F; e += blockDim.x) {           // modes added in order
+      const int rr2 = e / F, c = e % F;
+      const float2* red = Sst + (buf * V + rr2 * M) * RR + c;
+      float2 sum = red[0];
+      for (int mm = 1; mm < M; ++mm) sum = cadd(sum, red[mm * RR]);
+      dst[e] = sum;
+    }
+    b = bn;
+  }
+  float2* g = gPs + (long long)split * gp_stride + ((long long)(l * M + m) * F + r) * F;
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) {
+    const int c = t + 32 * n2;
+    g[c] = cadd(g[c], acc[n2]);
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // forward row pass over all modes of one wavelength (one mode chunk holds every mode).
 // Vector v = rr*M + m takes row r = blockIdx.x*rpb + rr of probe mode (l, m); its probe row
@@ -1212,6 +1300,68 @@ k_row_fwd_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
     float2* out = S + (((long long)b * a.C + cm) * F + r) * F;
 #pragma unroll
     for (int sl = 0; sl < N2; ++sl) out[idxO<F>(t, sl)] = v[sl];
+    b = bn;
+  }
+}
+
+// Same pass at F = 512 with one warp per row (fft512_fwd_warp): the probe row takes 16 values per
+// lane in registers instead of 32, so two blocks of up to 10 warps fit on an SM.
+// grid (512/rpb, L, nsplit), block 32*M*rpb <= kRowAdjWThreads, dynamic smem row_fwd_w_smem(M, rpb)
+__host__ __device__ constexpr int row_fwd_w_smem(int M, int rpb) {
+  return (M * rpb * kFft512WarpXchF + 2 * rpb * 512) * (int)sizeof(float2);
+}
+
+template <int F>
+__global__ void __launch_bounds__(kRowAdjWThreads, 2)
+k_row_fwd_w(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S, KArgs a, int rpb,
+            int nsplit) {
+  static_assert(F == 512, "one warp per row is the 512-point layout");
+  pdl_wait();
+  pdl_trigger();
+  constexpr int RR = kFft512WarpXchF;
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ int2 spos[kMaxB];
+  __shared__ float ssig[kMaxB];
+  const int M = a.M, V = M * rpb;
+  float2* xch = smem;                                 // [V][RR]
+  float2* Ost = xch + V * RR;                         // [2][rpb][F]
+  const int vec = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int rr = vec / M, m = vec % M;
+  const int row0 = blockIdx.x * rpb, r = row0 + rr;
+  const int l = blockIdx.y, split = blockIdx.z;
+  const int cm = l * M + m - a.chunk_base;
+  stage_batch(a, l, spos, ssig);
+  float2 pr[16];
+  {
+    const float2* Prow = P + ((long long)(l * M + m) * F + r) * F;
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) pr[n2] = __ldg(Prow + t + 32 * n2);
+  }
+  const float2* Ol = O + a.obj_off[l];
+  const int Wl = a.obj_w[l];
+  const int oc = (t & 15) + 256 * (t >> 4);           // output column of x[0] (then + 16 j)
+  int b = next_pos(spos, split - nsplit, a.nb, nsplit);
+  if (b >= 0) {
+    prefetch_orows<F>(Ol, Wl, spos[b], row0, rpb, Ost);
+    cp_async_commit();
+  }
+  for (int buf = 0; b >= 0; buf ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();                                  // position b's rows have landed; buf^1 is free
+    const int bn = next_pos(spos, b, a.nb, nsplit);
+    if (bn >= 0) {
+      prefetch_orows<F>(Ol, Wl, spos[bn], row0, rpb, Ost + (buf ^ 1) * rpb * F);
+      cp_async_commit();
+    }
+    const float s = ssig[b];
+    const float2* orow = Ost + (buf * rpb + rr) * F;
+    float2 v[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) v[n2] = cmul(pr[n2], cscale(orow[t + 32 * n2], s));
+    fft512_fwd_warp(v, t, xch + vec * RR, a.tw);
+    float2* out = S + (((long long)b * a.C + cm) * F + r) * F + oc;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) out[16 * j] = v[j];
     b = bn;
   }
 }

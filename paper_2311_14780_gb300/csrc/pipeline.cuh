@@ -107,6 +107,10 @@ int prepare_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_l<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_fwd_l<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  if constexpr (F == 512) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_w<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_fwd_w<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+  }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
@@ -290,7 +294,18 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
           continue;
         }
       }
-      if (fwd_l)
+      bool warp_rows_fwd = false;
+      if constexpr (F == 512) {
+        if (fwd_l && p.fwd_l_w) {
+          PTY_LAUNCH(p, kRowFwd, cs,
+                     launch_pdl(k_row_fwd_w<F>, dim3(F / p.rpb_adj, p.L, p.nsplit_fwd), 32 * p.M * p.rpb_adj,
+                                row_fwd_w_smem(p.M, p.rpb_adj), cs, c.O, c.P, S, a, p.rpb_adj, p.nsplit_fwd));
+          warp_rows_fwd = true;
+        }
+      }
+      if (warp_rows_fwd)
+        ;
+      else if (fwd_l)
         PTY_LAUNCH(p, kRowFwd, cs,
                    launch_pdl(k_row_fwd_l<F>, dim3(F / p.rpb_adj, p.L, p.nsplit_fwd), FftShape<F>::N1 * p.M * p.rpb_adj,
                               row_fwd_l_smem<F>(p.M, p.rpb_adj), cs, c.O, c.P, S, a, p.rpb_adj, p.nsplit_fwd));
@@ -387,7 +402,19 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
         return PTYCHO_ECUDA;
       if (adj_l) {
         constexpr int T = FftShape<F>::N1;
-        if (p.adj_l_pl2)
+        bool warp_rows = false;
+        if constexpr (F == 512) {
+          if (p.adj_l_w) {
+            PTY_LAUNCH(p, kRowAdj, cs,
+                       launch_pdl(k_row_adj_w<F>, dim3(F / p.rpb_adj, p.L, nsplit), 32 * p.M * p.rpb_adj,
+                                  row_adj_w_smem(p.M, p.rpb_adj), cs, c.O, c.P, S, gPs, (long long)p.P_numel, a,
+                                  p.rpb_adj, nsplit));
+            warp_rows = true;
+          }
+        }
+        if (warp_rows)
+          ;
+        else if (p.adj_l_pl2)
           PTY_LAUNCH(p, kRowAdj, cs,
                      launch_pdl(k_row_adj_l<F, true>, dim3(F / p.rpb_adj, p.L, nsplit), T * p.M * p.rpb_adj,
                                 row_adj_l_smem<F>(p.M, p.rpb_adj, true), cs, c.O, c.P, S, gPs, (long long)p.P_numel,

@@ -38,6 +38,8 @@ struct ptycho_plan {
   int adj_l = 0, rpb_adj = 1, nsplit_adj = 1;
   int adj_l_ok = 0;                            // k_row_adj_l can run (all modes fit a block and the scratch)
   int adj_l_pl2 = 0;                           // its probe rows through L1/L2, two blocks per SM
+  int adj_l_w = 0;                             // F = 512: one warp per row (k_row_adj_w)
+  int fwd_l_w = 0;                             // F = 512: one warp per row (k_row_fwd_w)
   // forward row pass over all modes of a wavelength per block (k_row_fwd_l), same rows per block
   int fwd_l = 0, nsplit_fwd = 1;
   // staged column passes (k_col_fwd_s / k_col_adj_s): one block per W columns of a position

@@ -580,6 +580,12 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
         const bool pl2_fits = T * g->M * rpb <= ptycho::kRowAdjL2Threads;
         p->adj_l_pl2 = pl2_fits && !(g->flags & PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM) &&
                        (F == 512 || (g->flags & PTYCHO_FLAG_ROW_ADJ_PROBE_L2));
+        // one warp per row at F = 512 (half the registers per thread, two 10-warp blocks per SM):
+        // measured 144.0 vs 153.3 ms per step on 512^2 x 6 wavelengths x 10 modes
+        p->adj_l_w = F == 512 && 32 * g->M * rpb <= ptycho::kRowAdjWThreads &&
+                     ptycho::row_adj_w_smem(g->M, rpb) <= ptycho::kRowAdjLSmemMax &&
+                     !(g->flags & (PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM | PTYCHO_FLAG_ROW_ADJ_PROBE_L2 |
+                                   PTYCHO_FLAG_ROWS_16_THREADS));
         // enough blocks for three per SM: split the batch's positions, each split summing its
         // probe gradient into a buffer of its own (bounded to 512 MB in all)
         const long long base = (long long)(F / rpb) * g->L;
@@ -596,6 +602,10 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
         if (((g->flags & PTYCHO_FLAG_FUSED_ROW_FWD) && !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_FWD)) || fwd_default) {
           p->fwd_l = 1;
           p->nsplit_fwd = (int)std::max<long long>(1, std::min<long long>((4ll * p->sms + base - 1) / base, p->B));
+          // one warp per row at F = 512 (opt-in): measured 146.4 vs 144.0 ms per step on 512^2 x
+          // 6 wavelengths x 10 modes, the pass itself shorter but the other streams' passes longer
+          p->fwd_l_w = F == 512 && 32 * g->M * rpb <= ptycho::kRowAdjWThreads &&
+                       (g->flags & PTYCHO_FLAG_FWD_ROWS_WARP) && !(g->flags & PTYCHO_FLAG_ROWS_16_THREADS);
         }
       }
     }

@@ -144,19 +144,65 @@ def strong_z(F):
     return F * 15e-6 / 0.5
 
 
-@pytest.mark.parametrize("flags", [0, 32, 4096, 8192])
+@pytest.mark.parametrize("flags", [0, 32, 2048, 4096, 8192, 16384, 32768])
 def test_fused_row_adjoint_at_512_with_eight_modes(dev, flags):
     """F = 512 with 8 modes takes the fused row passes (all modes of a wavelength per block:
-    forward rows with the probe row in registers; adjoint rows with the object-gradient rows
-    summed over the modes in shared memory and the probe rows through L1/L2); flag 32 forces the
-    per-mode row adjoint, 4096 the row adjoint that holds the probe rows in shared memory, 8192
-    the per-position forward row pass.  Several position batches and splits."""
+    forward rows with the probe row in registers, 16 threads per row; adjoint rows with one warp
+    per row, the object-gradient rows summed over the modes in shared memory and the probe rows
+    through L1/L2); flag 32 forces the per-mode row adjoint, 2048 the 16-thread adjoint rows with
+    the probe rows through L1/L2, 4096 the 16-thread adjoint rows that hold the probe rows in
+    shared memory, 8192 the per-position forward row pass, 16384 16 threads per row in both fused
+    passes, 32768 one warp per row in the forward too.  Several position batches and splits."""
     w = syn.tiny_workload(F=512, L=1, M=8, n_side=3, step=64, seed=77, remap=True, loss="poisson",
                           with_sigma=True, with_bg=True)
     case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=12)
     plan = case.plan(flags=flags, scratch_bytes=3 * 8 * 512 * 512 * 8)
     assert_ok(check_all(case, plan))
     assert_ok(check_all(case, plan, frames=[7, 0, 4]))
+    plan.close()
+
+
+def test_row_adjoint_one_warp_per_row_ten_modes_two_wavelengths(dev):
+    """The one-warp-per-row adjoint at 512^2 with the full block of 10 modes (320 threads), two
+    wavelengths, a ragged last batch, against the oracle and against the 16-thread row adjoint
+    (same arithmetic in another order: equal to rounding)."""
+    w = syn.tiny_workload(F=512, L=2, M=10, n_side=3, step=64, seed=78, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=15)
+    sb = 4 * 20 * 512 * 512 * 8                           # 4 positions per batch: 4 + 4 + 1
+    plan_w = case.plan(scratch_bytes=sb)
+    assert_ok(check_all(case, plan_w))
+    plan_d = case.plan(flags=2048, scratch_bytes=sb)
+    La, gO, gP = plan_w.adjoint(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t)
+    Lb, gOb, gPb = plan_d.adjoint(case.O, case.P, case.Im, case.sig_t, case.bg_t, case.mask_t)
+    assert max_rel(gO.cpu().numpy(), gOb.cpu().numpy()) < TOL_G_MAX
+    assert max_rel(gP.cpu().numpy(), gPb.cpu().numpy()) < TOL_G_MAX
+    assert plan_w.status() == 0
+    plan_w.close()
+    plan_d.close()
+
+
+@pytest.mark.parametrize("M", [4, 5])
+@pytest.mark.parametrize("flags", [0, 32768])
+def test_fused_forward_rows_at_512_with_four_and_five_modes(dev, M, flags):
+    """From 4 modes at 512^2 the forward row pass takes all modes of a wavelength per block, 16
+    threads per row, or with 32768 one warp per row (two rows of 4 modes per block: 256 threads;
+    one row of 5 modes: 160).  Two wavelengths, several position batches."""
+    w = syn.tiny_workload(F=512, L=2, M=M, n_side=3, step=64, seed=90 + M, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=M + flags)
+    plan = case.plan(flags=flags, scratch_bytes=4 * 2 * M * 512 * 512 * 8)
+    assert_ok(check_all(case, plan))
+    plan.close()
+
+
+def test_row_adjoint_one_warp_per_row_with_offsets(dev):
+    """The one-warp-per-row adjoint reads the shifted object patches when offsets are registered."""
+    w = syn.tiny_workload(F=512, L=1, M=8, n_side=3, step=64, seed=79, remap=True, loss="poisson",
+                          with_sigma=True, with_bg=True)
+    case = Case(w, dev, z=strong_z(512), mask_kind="shared", seed=16)
+    plan = case.plan()
+    _assert_offsets_ok(_offset_errors(case, plan, _offsets(w, 512)))
     plan.close()
 
 
