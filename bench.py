@@ -260,10 +260,13 @@ def run_reference(args, rank: int, world: int):
 # our arm
 # --------------------------------------------------------------------------------------
 def kernel_hash() -> str:
-    """sha256 prefix of the kernel sources (the device code the ncu counters belong to)."""
+    """sha256 prefix of every CUDA source of the library (the device code the ncu counters belong to)."""
     h = hashlib.sha256()
-    for f in ("fft_regs.cuh", "kernels.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2311_14780_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2311_14780_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

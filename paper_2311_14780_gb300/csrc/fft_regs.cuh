@@ -229,8 +229,8 @@ __device__ __forceinline__ void fft_inv_O2I(float2 (&x)[FftShape<F>::N2], int t,
 // and the pair (u, u ^ 16) combines E + T and E - T through a shuffle, giving Y[c][t] for
 // t = j + 16 q.  Each element is multiplied by W512^(-t c) (the F = 512 table entry tw[t*16 + c]),
 // the 16 x 32 block is transposed through ``xc`` (element (c, t) at c*33 + t: conflict-free in
-// both directions), and lane t takes a 16-point inverse DFT over c.  ``spec`` may alias ``xc`` (the spectrum is
-// read before the first write).  Out: x[n2] = value at n = lane + 32 n2 (layout I of 32 lanes).
+// both directions), and lane t takes a 16-point inverse DFT over c.  ``spec`` may alias ``xc``
+// (the spectrum is read before the first write).  Out: x[n2] = value at n = lane + 32 n2.
 __device__ __forceinline__ void fft512_inv_warp(const float2* spec, float2 (&x)[16], int lane, float2* xc,
                                                 const float2* __restrict__ tw) {
   constexpr int R = 33;

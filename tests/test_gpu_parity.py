@@ -227,7 +227,7 @@ def test_options_remap_mask(dev, remap, mask_kind):
     plan.close()
 
 
-@pytest.mark.parametrize("F", [64, 256])
+@pytest.mark.parametrize("F", [64, 256, 512])
 def test_recompute_mode_and_ragged_batches(dev, F):
     """Tiny scratch budgets force mode chunks (fields recomputed) and ragged position batches."""
     w = syn.tiny_workload(F=F, L=2, M=3, n_side=3, step=F // 8, seed=9, remap=True, loss="amplitude",
