@@ -87,6 +87,10 @@ extern "C" {
  *   measured 6 % faster on 512^2 x 10 modes x 6 wavelengths than 16 threads per row.  This flag
  *   keeps 16 threads per row in both fused row passes (so do ROW_ADJ_PROBE_L2 and
  *   ROW_ADJ_PROBE_SMEM for the adjoint).
+ * COLS_ONE_BLOCK: at F = 512 the TMA-staged column passes (without KEEP_PSI) transpose in two
+ *   halves through an exchange area of half the size and the adjoint reads its dL/dI factors
+ *   through L1/L2, so two blocks fit on an SM (99 KB of shared memory each); this flag keeps the
+ *   one-block passes (full exchange, staged factors).
  * FWD_ROWS_WARP: at F = 512 the fused forward row pass with one warp per row as well (when
  *   32*M*rpb <= 320).  Measured 1.7 % slower per step on 512^2 x 10 modes x 6 wavelengths (146.4
  *   vs 144.0 ms): its twice as many resident warps take the SMs from the other streams' passes.
@@ -119,6 +123,7 @@ extern "C" {
 #define PTYCHO_FLAG_UNFUSED_ROW_FWD 8192
 #define PTYCHO_FLAG_ROWS_16_THREADS 16384
 #define PTYCHO_FLAG_FWD_ROWS_WARP 32768
+#define PTYCHO_FLAG_COLS_ONE_BLOCK 65536
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */

@@ -220,6 +220,55 @@ __device__ __forceinline__ void fft_inv_O2I(float2 (&x)[FftShape<F>::N2], int t,
   Dft<N2, 1, true>::run(x);
 }
 
+// The same two transforms for N2 = 2 N1 (F = 512) with an exchange region of half the size: the
+// transpose goes in two halves (rows k2 < N1, then k2 >= N1), two more barriers per transform.
+// ``xc`` holds N1 x (N1 + 1) elements (XchHalf<F>).  Same arithmetic, same results.
+template <int F>
+struct XchHalf {
+  static constexpr int N1 = FftShape<F>::N1;
+  static constexpr int region_cols = (N1 * (N1 + 1)) | 1;
+};
+
+template <int F, class Sync>
+__device__ __forceinline__ void fft_fwd_I2O_half(float2 (&x)[FftShape<F>::N2], int t, float2* xc,
+                                                 const float2* __restrict__ tw, Sync sync) {
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2;
+  static_assert(N2 == 2 * N1, "two halves of N1 rows");
+  Dft<N2, 1, false>::run(x);
+  apply_twiddles<F, false>(x, t, tw);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int k = 0; k < N1; ++k) xc[k * (N1 + 1) + t] = x[h * N1 + k];       // rows k2 = h*N1 + k
+    sync();
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) x[h * N1 + n1] = xc[t * (N1 + 1) + n1];  // row k2 = t + N1*h
+    sync();
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) Dft<N1, 1, false>::run(x + q * N1);
+}
+
+template <int F, class Sync>
+__device__ __forceinline__ void fft_inv_O2I_half(float2 (&x)[FftShape<F>::N2], int t, float2* xc,
+                                                 const float2* __restrict__ tw, Sync sync) {
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2;
+  static_assert(N2 == 2 * N1, "two halves of N1 rows");
+#pragma unroll
+  for (int q = 0; q < 2; ++q) Dft<N1, 1, true>::run(x + q * N1);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) xc[t * (N1 + 1) + n1] = x[h * N1 + n1];  // row k2 = t + N1*h
+    sync();
+#pragma unroll
+    for (int k = 0; k < N1; ++k) x[h * N1 + k] = xc[k * (N1 + 1) + t];       // rows k2 = h*N1 + k
+    sync();
+  }
+  apply_twiddles<F, true>(x, t, tw);
+  Dft<N2, 1, true>::run(x);
+}
+
 // Inverse (unscaled, the adjoint of the forward DFT) 512-point transform by a whole warp, 16 values
 // per lane, for kernels that hold a spectrum row in shared memory in natural order.  With
 // n = t + 32 n2 and k = c + 16 k1 (t, lane in [0, 32); c, n2 in [0, 16); k1 in [0, 32)):

@@ -862,6 +862,118 @@ k_col_adj_tma(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, K
   if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, phase, a.status);
 }
 
+// TMA-staged column passes with the half-size exchange (fft_*_half; F = 512) and, in the adjoint,
+// the dL/dI factors read through L1/L2 instead of being staged: 99 KB of shared memory per block
+// instead of 134 / 166 KB, so two 8-warp blocks fit on an SM.  Same arithmetic as
+// k_col_fwd_tma / k_col_adj_tma without STORE.   grid (F/W, G, nb)
+template <int F> struct ColTma2 {
+  static constexpr int W = ColCfg<F>::W;
+  static constexpr int smem = ColTma<F>::stage_bytes + W * XchHalf<F>::region_cols * (int)sizeof(float2) + 16 + 128;
+};
+
+template <int F>
+__global__ void __launch_bounds__(ColCfg<F>::threads, 2)
+k_col_fwd_tma2(const __grid_constant__ CUtensorMap map, float* __restrict__ Ipart, KArgs a, int first_chunk) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W, R = XchHalf<F>::region_cols;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* stage = align_tma_stage(smem_raw);
+  float2* xch = stage + F * W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + W * R);
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int col0 = blockIdx.x * W, col = col0 + c;
+  const int g = blockIdx.y, b = blockIdx.z;
+  const int m0 = g * a.MG, m1 = min(a.chunk_len, m0 + a.MG);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && m0 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + m0) * F, bar);
+  float acc[N2];
+#pragma unroll
+  for (int i = 0; i < N2; ++i) acc[i] = 0.f;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int cm = m0; cm < m1; ++cm) {
+    ok = __syncthreads_and(mbar_wait_bounded(bar, phase, a.status));
+    if (!ok) break;
+    phase ^= 1;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = stage[(t + N1 * n2) * W + c];
+    __syncthreads();                           // the stage is free for the next mode
+    if (threadIdx.x == 0 && cm + 1 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + cm + 1) * F, bar);
+    fft_fwd_I2O_half<F>(v, t, xch + c * R, a.tw, BlockSync{});
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) acc[sl] = fmaf(v[sl].x, v[sl].x, fmaf(v[sl].y, v[sl].y, acc[sl]));
+  }
+  if (!ok) {                                   // give a lost copy a bounded chance to land, then stop
+    if (threadIdx.x == 0) mbar_wait_bounded(bar, phase, a.status);
+    return;
+  }
+  const float inv = 1.0f / (float)F;
+  float* dst = Ipart + ((long long)b * a.G + g) * F * F;
+  const int cc = (col + F / 2) & (F - 1);
+#pragma unroll
+  for (int sl = 0; sl < N2; ++sl) {
+    const int rc = (idxO<F>(t, sl) + F / 2) & (F - 1);
+    float val = acc[sl] * (inv * inv);
+    if (!first_chunk) val += dst[rc * F + cc];
+    dst[rc * F + cc] = val;
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(ColCfg<F>::threads, 2)
+k_col_adj_tma2(const __grid_constant__ CUtensorMap map, float2* __restrict__ S, KArgs a, AdjArgs aa) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, W = ColCfg<F>::W, R = XchHalf<F>::region_cols;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* stage = align_tma_stage(smem_raw);
+  float2* xch = stage + F * W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + W * R);
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int col0 = blockIdx.x * W, col = col0 + c;
+  const int g = blockIdx.y, b = blockIdx.z;
+  const int m0 = g * a.MG, m1 = min(a.chunk_len, m0 + a.MG);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && m0 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + m0) * F, bar);
+  // this thread's column of the dL/dI factors (DC-centred storage), read per mode through L1/L2
+  const float* Gc = (aa.remap ? aa.Gt : aa.D) + (long long)b * F * F + ((col + F / 2) & (F - 1));
+  const float scale = 2.0f / (float)F;
+  const float inv = 1.0f / (float)F;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int cm = m0; cm < m1; ++cm) {
+    ok = __syncthreads_and(mbar_wait_bounded(bar, phase, a.status));
+    if (!ok) break;
+    phase ^= 1;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = stage[(t + N1 * n2) * W + c];
+    __syncthreads();                           // the stage is free for the next mode
+    if (threadIdx.x == 0 && cm + 1 < m1) col_tma_issue<F>(stage, &map, col0, ((long long)b * a.C + cm + 1) * F, bar);
+    fft_fwd_I2O_half<F>(v, t, xch + c * R, a.tw, BlockSync{});
+#pragma unroll
+    for (int sl = 0; sl < N2; ++sl) {
+      const float gk = __ldg(Gc + (long long)((idxO<F>(t, sl) + F / 2) & (F - 1)) * F) * scale;
+      v[sl] = cscale(cscale(v[sl], inv), gk);
+    }
+    fft_inv_O2I_half<F>(v, t, xch + c * R, a.tw, BlockSync{});
+    float2* base = S + ((long long)b * a.C + cm) * F * F + col;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) base[(long long)(t + N1 * n2) * F] = v[n2];
+  }
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, phase, a.status);
+}
+
 // ---------------------------------------------------------------------------------------
 // adjoint row pass: chi = dL/dpsi; probe gradient summed over the batch; object-gradient
 // contributions conj(sigma P) chi left in S (or, with ATOMIC, added to grad O with FP32

@@ -110,6 +110,8 @@ int prepare_kernels() {
   if constexpr (F == 512) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_adj_w<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_fwd_w<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowAdjLSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_fwd_tma2<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma2<F>::smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_col_adj_tma2<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, ColTma2<F>::smem);
   }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shift_rows<F, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowCfg<F>::smem);
@@ -316,6 +318,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       if (col_staged) {
         rc = narrow ? launch_cols_s<F, 4>(p, true, store, cs, S, Ip, a, aa) : launch_cols_s<F, 0>(p, true, store, cs, S, Ip, a, aa);
         if (rc) return rc;
+      } else if (F == 512 && p.has_tma && p.col_tma2 && !store) {
+        if constexpr (F == 512)
+          PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma2<F>, col_grid, col_blk, ColTma2<F>::smem, cs,
+                                                p.tmap_S[set], Ip, a, (int)(ch == 0)));
       } else if (p.has_tma && store)
         PTY_LAUNCH(p, kColFwd, cs, launch_pdl(k_col_fwd_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_fwd, cs,
                                               p.tmap_S[set], S, Ip, a, (int)(ch == 0)));
@@ -383,6 +389,10 @@ int run_pipeline(ptycho_plan& p, const CallArgs& c, cudaStream_t st) {
       if (col_staged) {
         rc = narrow ? launch_cols_s<F, 4>(p, false, store, cs, S, Ip, a, aa) : launch_cols_s<F, 0>(p, false, store, cs, S, Ip, a, aa);
         if (rc) return rc;
+      } else if (F == 512 && p.has_tma && p.col_tma2 && !store) {
+        if constexpr (F == 512)
+          PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_tma2<F>, col_grid, col_blk, ColTma2<F>::smem, cs,
+                                                p.tmap_S[set], S, a, aa));
       } else if (p.has_tma && store)
         PTY_LAUNCH(p, kColAdj, cs, launch_pdl(k_col_adj_tma<F, true>, col_grid, col_blk, ColTma<F>::smem_adj, cs,
                                               p.tmap_S[set], S, a, aa));

@@ -40,6 +40,7 @@ struct ptycho_plan {
   int adj_l_pl2 = 0;                           // its probe rows through L1/L2, two blocks per SM
   int adj_l_w = 0;                             // F = 512: one warp per row (k_row_adj_w)
   int fwd_l_w = 0;                             // F = 512: one warp per row (k_row_fwd_w)
+  int col_tma2 = 0;                            // F = 512: staged columns, half exchange, two blocks per SM
   // forward row pass over all modes of a wavelength per block (k_row_fwd_l), same rows per block
   int fwd_l = 0, nsplit_fwd = 1;
   // staged column passes (k_col_fwd_s / k_col_adj_s): one block per W columns of a position

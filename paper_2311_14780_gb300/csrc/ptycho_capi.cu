@@ -698,6 +698,8 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
     // at F = 256 and F = 64 they measured slower or equal)
     const bool tma_default = (F >= 512 && p->C >= 2) || (F == 128 && p->C >= 4);
     p->has_tma = (g->flags & PTYCHO_FLAG_NO_TMA) || p->czt ? 0 : ((g->flags & PTYCHO_FLAG_TMA) || tma_default) ? 1 : 0;
+    // F = 512: the staged column passes with the half-size exchange, two blocks per SM
+    p->col_tma2 = F == 512 && !(g->flags & PTYCHO_FLAG_COLS_ONE_BLOCK) ? 1 : 0;
     for (int i = 0; i < p->nsets; ++i)
       if (p->has_tma && !make_column_map(&p->tmap_S[i], p->d_S + (long long)i * p->B * p->C * FF, F, rows, W))
         p->has_tma = 0;

@@ -144,7 +144,7 @@ def strong_z(F):
     return F * 15e-6 / 0.5
 
 
-@pytest.mark.parametrize("flags", [0, 32, 2048, 4096, 8192, 16384, 32768])
+@pytest.mark.parametrize("flags", [0, 32, 2048, 4096, 8192, 16384, 32768, 65536])
 def test_fused_row_adjoint_at_512_with_eight_modes(dev, flags):
     """F = 512 with 8 modes takes the fused row passes (all modes of a wavelength per block:
     forward rows with the probe row in registers, 16 threads per row; adjoint rows with one warp
@@ -152,7 +152,8 @@ def test_fused_row_adjoint_at_512_with_eight_modes(dev, flags):
     through L1/L2); flag 32 forces the per-mode row adjoint, 2048 the 16-thread adjoint rows with
     the probe rows through L1/L2, 4096 the 16-thread adjoint rows that hold the probe rows in
     shared memory, 8192 the per-position forward row pass, 16384 16 threads per row in both fused
-    passes, 32768 one warp per row in the forward too.  Several position batches and splits."""
+    passes, 32768 one warp per row in the forward too, 65536 the one-block TMA column passes (full
+    exchange area, staged dL/dI factors).  Several position batches and splits."""
     w = syn.tiny_workload(F=512, L=1, M=8, n_side=3, step=64, seed=77, remap=True, loss="poisson",
                           with_sigma=True, with_bg=True)
     case = Case(w, dev, z=strong_z(512), mask_kind="frame", seed=12)
