@@ -63,14 +63,14 @@ extern "C" {
  *   for F = 128 when a position has at least four fields (L*M >= 4), where it measured
  *   faster; otherwise the larger shared-memory footprint costs more occupancy than the
  *   copies save.  NO_TMA wins when both are given.
- * UNFUSED_ROW_ADJ: one block of the adjoint row pass per probe mode, each mode's object-
- *   gradient row left in the scratch for the object-gradient kernel (always the case for
- *   F = 512 with fewer than 8 modes).  The default for F <= 256, and for F = 512 from 8 modes
- *   up, whenever all modes of a position fit the scratch and T*M <= 256 (T = 4, 8, 16, 16
- *   threads per row for F = 64, 128, 256, 512), takes all modes of a wavelength per block:
- *   the probe rows
- *   stay in shared memory for the batch and the object-gradient rows are summed over the
- *   modes before they are written.
+ * UNFUSED_ROW_ADJ / FUSED_ROW_ADJ: one block of the adjoint row pass per probe mode, each mode's
+ *   object-gradient row left in the scratch for the object-gradient kernel / all modes of a
+ *   wavelength per block, the probe rows read once per batch and the object-gradient rows summed
+ *   over the modes before they are written.  The fused pass needs all modes of a position in the
+ *   scratch and T*M <= 256 (T = 4, 8, 16, 16 threads per row for F = 64, 128, 256, 512; 32 with
+ *   one warp per row).  Default: fused for F <= 256; at F = 512 fused from 2 modes up where the
+ *   one-warp rows fit (M <= 10), and from 8 modes up otherwise; per mode with one mode (measured
+ *   5-9 % faster there).  UNFUSED_ROW_ADJ wins when both are given.
  * STAGED_COLUMNS: whenever all modes of a position fit the scratch, run each column block over
  *   all modes of W columns of one position, copying the next mode's columns into shared memory
  *   (cp.async, double-buffered) while the current one is transformed (one intensity slice, no
@@ -124,6 +124,7 @@ extern "C" {
 #define PTYCHO_FLAG_ROWS_16_THREADS 16384
 #define PTYCHO_FLAG_FWD_ROWS_WARP 32768
 #define PTYCHO_FLAG_COLS_ONE_BLOCK 65536
+#define PTYCHO_FLAG_FUSED_ROW_ADJ 131072
 
 #define PTYCHO_LOSS_AMPLITUDE 0  /* sum (sqrt(I + eps) - sqrt(Ihat))^2                  */
 #define PTYCHO_LOSS_POISSON 1    /* sum (I + eps) - Ihat - Ihat log((I + eps) / Ihat)   */

@@ -558,10 +558,11 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
       case 256: T = ptycho::FftShape<256>::N1; break;
       default: T = ptycho::FftShape<512>::N1; break;
     }
-    // measured: at F = 512 the fused kernel's registers (two 32-value rows per thread) cost
-    // more occupancy than the probe reuse saves with few modes (4 modes x 3 wavelengths: 8 %
-    // slower), but from 8 modes up the object-gradient kernel's M-fold smaller read wins (8 x 3:
-    // 2 % faster; 10 modes x 6 wavelengths, 512^2: 7 %), so F = 512 fuses from M = 8
+    // measured at F = 512: with 16 threads per row the fused kernel's registers (two 32-value rows
+    // per thread) cost more occupancy than the probe reuse saves below 8 modes (4 modes x 3
+    // wavelengths: 8 % slower; from 8 modes up faster: 8 x 3 by 2 %, 10 x 6 by 7 %); with one warp
+    // per row it is faster from 2 modes up (2 x 3: 9.44 vs 9.76 ms, 4 x 3: 14.47 vs 17.32, 6 x 3:
+    // 19.56 vs 24.81, 7 x 2: 16.35 vs 19.60) and slower with one mode (1 x 3: 6.67 vs 6.35)
     if (p->store && T * g->M <= 256) {
       int rpb = 1;
       while (2 * rpb * T * g->M <= 128 && 2 * rpb <= F) rpb *= 2;
@@ -573,19 +574,20 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
       }
       if (smem <= ptycho::kRowAdjLSmemMax) {
         p->adj_l_ok = 1;
-        p->adj_l = !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) && (F <= 256 || g->M >= 8);
         p->rpb_adj = rpb;
-        // probe rows through L1/L2 and two blocks per SM: measured 1.4 % faster on config 4 (175.8
-        // vs 178.2 ms per step) and 2.9 % on 512^2 x 8 modes x 3 wavelengths; equal on config 2
-        const bool pl2_fits = T * g->M * rpb <= ptycho::kRowAdjL2Threads;
-        p->adj_l_pl2 = pl2_fits && !(g->flags & PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM) &&
-                       (F == 512 || (g->flags & PTYCHO_FLAG_ROW_ADJ_PROBE_L2));
         // one warp per row at F = 512 (half the registers per thread, two 10-warp blocks per SM):
         // measured 144.0 vs 153.3 ms per step on 512^2 x 6 wavelengths x 10 modes
         p->adj_l_w = F == 512 && 32 * g->M * rpb <= ptycho::kRowAdjWThreads &&
                      ptycho::row_adj_w_smem(g->M, rpb) <= ptycho::kRowAdjLSmemMax &&
                      !(g->flags & (PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM | PTYCHO_FLAG_ROW_ADJ_PROBE_L2 |
                                    PTYCHO_FLAG_ROWS_16_THREADS));
+        p->adj_l = !(g->flags & PTYCHO_FLAG_UNFUSED_ROW_ADJ) &&
+                   (F <= 256 || g->M >= 8 || (p->adj_l_w && g->M >= 2) || (g->flags & PTYCHO_FLAG_FUSED_ROW_ADJ));
+        // probe rows through L1/L2 and two blocks per SM: measured 1.4 % faster on config 4 (175.8
+        // vs 178.2 ms per step) and 2.9 % on 512^2 x 8 modes x 3 wavelengths; equal on config 2
+        const bool pl2_fits = T * g->M * rpb <= ptycho::kRowAdjL2Threads;
+        p->adj_l_pl2 = pl2_fits && !(g->flags & PTYCHO_FLAG_ROW_ADJ_PROBE_SMEM) &&
+                       (F == 512 || (g->flags & PTYCHO_FLAG_ROW_ADJ_PROBE_L2));
         // enough blocks for three per SM: split the batch's positions, each split summing its
         // probe gradient into a buffer of its own (bounded to 512 MB in all)
         const long long base = (long long)(F / rpb) * g->L;
