@@ -260,18 +260,19 @@ def run_reference(args, rank: int, world: int):
 # our arm
 # --------------------------------------------------------------------------------------
 def kernel_hash() -> str:
-    """sha256 prefix of every CUDA source of the library (the device code the ncu counters belong to)."""
+    """sha256 prefix of the library's kernel headers (every ``csrc/*.cuh``: the device code and its launches)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_14780_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith(".cuh"):
             h.update(f.encode())
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+def ncu_traffic(kernel: str, workload: str, units_per_launch: float):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels and on launches of
+    the same size (evaluations per launch within 5 %)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
@@ -279,6 +280,9 @@ def ncu_traffic(kernel: str, workload: str):
         return None
     e = d.get(f"{workload}:{kernel}")
     if not e or d.get("kernel_sha") != kernel_hash():
+        return None
+    ev = e.get("evaluations_per_launch")
+    if not ev or abs(units_per_launch - ev) > 0.05 * ev:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -370,7 +374,7 @@ def kernel_profile(plan, step, evals: int, F: int, prof_steps: int, peak: float,
         per_launch_flops = 0.25 * flops_eval * units_per_launch
         achieved = per_launch_flops / (kern_ms / kern_n / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(dom, traffic_key), "peak_source": peak_src,
+                "frac": achieved / peak, "traffic": ncu_traffic(dom, traffic_key, units_per_launch), "peak_source": peak_src,
                 "units_per_launch": units_per_launch, "flops_per_unit": 0.25 * flops_eval,
                 "avg_launch_ms": kern_ms / kern_n,
                 "note": "launch durations are CUDA events on the launch stream with three position batches in "

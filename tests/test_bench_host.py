@@ -20,16 +20,19 @@ def test_algorithmic_flops_are_two_ffts_of_5_n_log2_n():
     assert bench.algorithmic_flops_per_eval(256) == pytest.approx(10.49e6, rel=1e-3)
 
 
-def test_traffic_is_reported_only_for_the_kernel_sources_it_was_measured_on(monkeypatch):
+def test_traffic_is_reported_only_for_the_kernel_sources_and_launch_size_it_was_measured_on(monkeypatch):
     import bench
     d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     monkeypatch.setattr(bench, "kernel_hash", lambda: d["kernel_sha"])
-    v = bench.ncu_traffic("col_adj", "config2")
+    ev = d["config2:col_adj"]["evaluations_per_launch"]
+    v = bench.ncu_traffic("col_adj", "config2", ev)
     assert v == d["config2:col_adj"]["dram_bytes_per_launch"] and v > 0
+    assert bench.ncu_traffic("col_adj", "config2", 0.97 * ev) == v          # a ragged last batch
+    assert bench.ncu_traffic("col_adj", "config2", 0.8 * ev) is None         # other launch sizes
     monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
-    assert bench.ncu_traffic("col_adj", "config2") is None
+    assert bench.ncu_traffic("col_adj", "config2", ev) is None
     monkeypatch.undo()
-    assert bench.ncu_traffic("no_such_kernel", "config2") is None
+    assert bench.ncu_traffic("no_such_kernel", "config2", ev) is None
 
 
 def test_camera_frames_are_seeded_and_hit_both_thresholds():
