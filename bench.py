@@ -89,8 +89,9 @@ def parse():
                          "(default: 5 at 512^2, 20 otherwise; 0 = skip)")
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests of the reduced serving stream appended to the default line (0 = none)")
-    ap.add_argument("--serve-mode", type=int, default=0,
-                    help="serving tick: 0 = one launch per pass over all sites, 1 = one child graph per site")
+    ap.add_argument("--serve-mode", type=int, default=1,
+                    help="serving tick: 0 = one launch per pass over all sites, 1 = one child graph per site "
+                         "(the library default); the default line also times the other form")
     ap.add_argument("--tick-evals", type=int, default=32768,
                     help="config5: admit while the active sites' evaluations per tick stay within this (0 = no cap)")
     return ap.parse_args()
@@ -648,12 +649,21 @@ def run_ours(args, rank: int, world: int):
         p_sum = plain_stream(plain_reqs)
         p_sum["final_loss_rel_diff_max"] = max(abs(a.final_loss - b.final_loss) / max(abs(b.final_loss), 1e-300)
                                                for a, b in zip(served, plain_reqs))
+        # the other tick form on a fresh copy of the same requests
+        other = 1 - args.serve_mode
+        served2, _ = serving_requests(sargs, dev)
+        o_sum = serve_stream(served2, int(args.budget_gb * (1 << 30)), max_tick_evals=args.tick_evals or None,
+                             mode=other)
         serving = {"stream": f"first {sargs.requests} requests of the config-5 stream (Poisson arrivals, mean 50 ms; "
                              f"F in {{128,256,512}}, J 100-900, L 1-5, M 1-8; {args.iterations} iterations each); "
                              "full stream: bench.py --config config5",
+                   "mode": SERVE_MODES[args.serve_mode],
                    "served": s_sum, "plain_one_site_at_a_time": p_sum,
                    "served_over_plain": s_sum["evals_per_s"] / p_sum["evals_per_s"],
-                   "site_iteration_ms_p50": s_sum["iter_ms_p50"], "site_iteration_ms_p99": s_sum["iter_ms_p99"]}
+                   "site_iteration_ms_p50": s_sum["iter_ms_p50"], "site_iteration_ms_p99": s_sum["iter_ms_p99"],
+                   "other_mode": {"mode": SERVE_MODES[other],
+                                  **{k: o_sum[k] for k in ("evals_per_s", "iter_ms_p50", "iter_ms_p99",
+                                                            "time_to_target_ms_p50", "time_to_target_ms_p99")}}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -672,6 +682,9 @@ def run_ours(args, rank: int, world: int):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+SERVE_MODES = {0: "shared launches (one launch per pass over all sites)", 1: "one child graph per site"}
 
 
 def serving_requests(args, dev):
@@ -728,7 +741,7 @@ def run_serving(args, rank: int, world: int):
                 "config": {"workload": f"config5: serving stream of {args.requests} requests, Poisson arrivals "
                                        f"(mean 50 ms), F in {{128,256,512}}, J in [100,900], L 1-5, M 1-8, "
                                        f"{args.iterations} iterations each, HBM budget {args.budget_gb} GB"},
-                "clocks": clk, "serving": s_sum, "plain": p_sum,
+                "clocks": clk, "mode": SERVE_MODES[args.serve_mode], "serving": s_sum, "plain": p_sum,
                 "served_over_plain": (s_sum["evals_per_s"] / p_sum["evals_per_s"]) if p_sum else None}
         print(json.dumps(line))
     return 0

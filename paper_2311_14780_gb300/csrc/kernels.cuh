@@ -65,6 +65,29 @@ struct KArgs {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// Whether launch_pdl asks for programmatic stream serialisation (per host thread; each
+// compute call sets it from its plan's flags).
+inline bool& pdl_enabled() {
+  static thread_local bool on = true;
+  return on;
+}
+
+// Launch with programmatic stream serialisation (see pdl_wait above).
+template <typename... KP, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
+}
+
 // Position index of batch entry i, or -1 (and the status bit set) if out of range.
 __device__ __forceinline__ int batch_pos(const KArgs& a, int i) {
   const int j = a.bidx[i];
@@ -1169,11 +1192,9 @@ __device__ __forceinline__ void prefetch_orows(const float2* __restrict__ Ol, in
 }
 
 template <int F, bool PL2>
-__global__ void __launch_bounds__(PL2 ? kRowAdjL2Threads : 256, (F <= 256 || PL2 ? 2 : 1))
-k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
-            float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void row_adj_l_body(const float2* __restrict__ O, const float2* __restrict__ P,
+                                               float2* __restrict__ S, float2* __restrict__ gPs, long long gp_stride,
+                                               const KArgs& a, int rpb, int nsplit, const uint3 bid) {
   constexpr int N1 = FftShape<F>::N1, N2 = FftShape<F>::N2, T = N1, RR = Xch<F>::region_rows;
   extern __shared__ __align__(16) float2 smem[];
   __shared__ int2 spos[kMaxB];
@@ -1185,8 +1206,8 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
   float2* Ost = Sst + 2 * V * RR;                     // [2][rpb][F] object rows
   const int vec = threadIdx.x / T, t = threadIdx.x % T;
   const int rr = vec / M, m = vec % M;
-  const int row0 = blockIdx.x * rpb, r = row0 + rr;
-  const int l = blockIdx.y, split = blockIdx.z;
+  const int row0 = bid.x * rpb, r = row0 + rr;
+  const int l = bid.y, split = bid.z;
   const int cm = l * M + m - a.chunk_base;
   const int slot0 = l * M - a.chunk_base;             // slot of the mode sum
   stage_batch(a, l, spos, ssig);
@@ -1263,6 +1284,15 @@ k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
   }
 }
 
+template <int F, bool PL2>
+__global__ void __launch_bounds__(PL2 ? kRowAdjL2Threads : 256, (F <= 256 || PL2 ? 2 : 1))
+k_row_adj_l(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
+            float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
+  pdl_wait();
+  pdl_trigger();
+  row_adj_l_body<F, PL2>(O, P, S, gPs, gp_stride, a, rpb, nsplit, blockIdx);
+}
+
 // Same pass at F = 512 with one warp per row (fft512_inv_warp: 16 values per lane instead of 32
 // per thread of a 16-thread vector), probe rows through L1/L2: the row and its probe-gradient
 // sums take half the registers, so twice as many warps fit on an SM.  Vector v (warp v) takes
@@ -1275,12 +1305,10 @@ __host__ __device__ constexpr int row_adj_w_smem(int M, int rpb) {
 }
 
 template <int F>
-__global__ void __launch_bounds__(kRowAdjWThreads, 2)
-k_row_adj_w(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
-            float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
+__device__ __forceinline__ void row_adj_w_body(const float2* __restrict__ O, const float2* __restrict__ P,
+                                               float2* __restrict__ S, float2* __restrict__ gPs, long long gp_stride,
+                                               const KArgs& a, int rpb, int nsplit, const uint3 bid) {
   static_assert(F == 512, "one warp per row is the 512-point layout");
-  pdl_wait();
-  pdl_trigger();
   constexpr int RR = kRowAdjWRegion;
   extern __shared__ __align__(16) float2 smem[];
   __shared__ int2 spos[kMaxB];
@@ -1290,8 +1318,8 @@ k_row_adj_w(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
   float2* Ost = Sst + 2 * V * RR;                     // [2][rpb][F] object rows
   const int vec = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int rr = vec / M, m = vec % M;
-  const int row0 = blockIdx.x * rpb, r = row0 + rr;
-  const int l = blockIdx.y, split = blockIdx.z;
+  const int row0 = bid.x * rpb, r = row0 + rr;
+  const int l = bid.y, split = bid.z;
   const int cm = l * M + m - a.chunk_base;
   const int slot0 = l * M - a.chunk_base;
   stage_batch(a, l, spos, ssig);
@@ -1349,6 +1377,15 @@ k_row_adj_w(const float2* __restrict__ O, const float2* __restrict__ P, float2* 
     const int c = t + 32 * n2;
     g[c] = cadd(g[c], acc[n2]);
   }
+}
+
+template <int F>
+__global__ void __launch_bounds__(kRowAdjWThreads, 2)
+k_row_adj_w(const float2* __restrict__ O, const float2* __restrict__ P, float2* __restrict__ S,
+            float2* __restrict__ gPs, long long gp_stride, KArgs a, int rpb, int nsplit) {
+  pdl_wait();
+  pdl_trigger();
+  row_adj_w_body<F>(O, P, S, gPs, gp_stride, a, rpb, nsplit, blockIdx);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1488,21 +1525,19 @@ __global__ void k_sum_splits(const float2* __restrict__ part, int nsplit, long l
 // their loads issued together.   grid (tiles of the largest box, L)
 // ---------------------------------------------------------------------------------------
 template <int F>
-__global__ void __launch_bounds__(256)
-k_obj_grad_l(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void obj_grad_l_body(const float2* __restrict__ S, float2* __restrict__ gO, const KArgs& a,
+                                                const uint3 bid) {
   __shared__ int2 spos[kMaxB];
   __shared__ float ssig[kMaxB];
   __shared__ int list[kMaxB];
   __shared__ int nlist;
-  const int l = blockIdx.y;
+  const int l = bid.y;
   const int by0 = a.box[l][0], bx0 = a.box[l][1];
   const int ntx = (a.box[l][3] - bx0 + kTile - 1) / kTile;
   const int nty = (a.box[l][2] - by0 + kTile - 1) / kTile;
-  if ((int)blockIdx.x >= ntx * nty) return;          // uniform over the block
+  if ((int)bid.x >= ntx * nty) return;          // uniform over the block
   stage_batch(a, l, spos, ssig);
-  const int oy0 = by0 + ((int)blockIdx.x / ntx) * kTile, ox0 = bx0 + ((int)blockIdx.x % ntx) * kTile;
+  const int oy0 = by0 + ((int)bid.x / ntx) * kTile, ox0 = bx0 + ((int)bid.x % ntx) * kTile;
   if (threadIdx.x < 32) {                             // ordered compaction by warp 0
     int n = 0;
     for (int b0 = 0; b0 < a.nb; b0 += 32) {
@@ -1557,6 +1592,14 @@ k_obj_grad_l(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
       *p = cadd(*p, acc[k]);
     }
   }
+}
+
+template <int F>
+__global__ void __launch_bounds__(256)
+k_obj_grad_l(const float2* __restrict__ S, float2* __restrict__ gO, KArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  obj_grad_l_body<F>(S, gO, a, blockIdx);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -20,29 +20,6 @@ namespace ptycho {
     prof_end((p), pty_ev, (st));                                     \
   } while (0)
 
-// Whether launch_pdl asks for programmatic stream serialisation (per host thread; each
-// compute call sets it from its plan's flags).
-inline bool& pdl_enabled() {
-  static thread_local bool on = true;
-  return on;
-}
-
-// Launch with programmatic stream serialisation (see pdl_wait in kernels.cuh).
-template <typename... KP, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KP>(args)...);
-}
-
 template <int F, int WN>
 cudaError_t set_cols_smem() {
   cudaError_t e = cudaFuncSetAttribute(k_col_fwd_s<F, true, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -68,7 +68,7 @@ class Server:
     SHARED_LAUNCHES = 0
     SITE_GRAPHS = 1
 
-    def __init__(self, budget_bytes: int, max_sites: int = 128, mode: int = 0):
+    def __init__(self, budget_bytes: int, max_sites: int = 128, mode: int = 1):
         h = ctypes.c_void_p()
         _check(_native.lib().ptycho_server_create(int(budget_bytes), int(max_sites), ctypes.byref(h)),
                "ptycho_server_create")
@@ -132,7 +132,7 @@ class Server:
 
 
 def serve_stream(reqs: List[Request], budget_bytes: int, max_sites: int = 128, realtime: bool = True,
-                 max_tick_evals: Optional[int] = None, mode: int = 0) -> dict:
+                 max_tick_evals: Optional[int] = None, mode: int = 1) -> dict:
     """Run the requests through a Server (``mode``: Server.SHARED_LAUNCHES or SITE_GRAPHS),
     admitting them as they arrive and fit.
 

@@ -108,10 +108,9 @@ def test_served_iterations_match_ptycho_step(mode, F):
     torch.cuda.synchronize()
     sv.release(slot)
     sv.close()
-    # the shared launches run the per-mode row adjoint (UNFUSED_ROW_ADJ = 32); at 512^2 with two modes
-    # the plan's default fuses the modes, which sums the object gradient in another order (2e-7
-    # relative), and three Adam steps grow that to 1e-4 on near-zero gradient entries
-    plan = plan_geometry_plan(r, flags=32 if (mode == 0 and F == 512) else 0)
+    # the shared launches run each site's row adjoint in its plan's variant (fused over the modes
+    # here, with the plan's position splits), so both forms match the plan's step
+    plan = plan_geometry_plan(r)
     st = AdamState(plan, r.lr_O, r.lr_P)
     for _ in range(3):
         plan.step(st, O0, P0, r.I_meas)
