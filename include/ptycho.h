@@ -154,8 +154,9 @@ typedef struct {
   int32_t loss;             /* PTYCHO_LOSS_AMPLITUDE, _POISSON or _POISSON_GAUSSIAN     */
   float eps;                /* intensity floor added to I in the loss and its gradient  */
   int64_t scratch_bytes;    /* FFT scratch budget in bytes; 0 = library default (about
-                               1200 evaluations per batch and at least three batches per
-                               call, at most 2 GiB per buffer set)                     */
+                               1200 evaluations but at least 64 positions per batch, at
+                               least three batches per call, batches of equal size within
+                               one position, at most 8 GiB per buffer set)              */
   int32_t overlap;          /* position batches in flight on separate streams (1..4), each
                                with its own scratch set; 0 = library default (3)       */
   int32_t flags;            /* PTYCHO_FLAG_* variants; 0 = defaults                      */

@@ -154,13 +154,22 @@ enum KernelKind { kRowFwd = 0, kColFwd, kLoss, kColAdj, kRowAdj, kObjGrad, kLoss
 long long prof_begin(ptycho_plan& p, int kind, cudaStream_t st);
 void prof_end(ptycho_plan& p, long long idx, cudaStream_t st);
 
-// ptycho_plan_create with a target of evaluations per position batch.
-int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** out);
+// How the default batching sizes a plan's position batches (ignored with an explicit scratch_bytes):
+// about ``evals`` evaluations per batch, but at least ``min_positions`` positions, with one buffer
+// set of at most ``max_set_bytes``.
+struct BatchTarget {
+  long long evals;
+  long long min_positions;
+  long long max_set_bytes;
+};
+// ptycho_plan_create with a batching target.
+int create_plan(const ptycho_geom_t* g, const BatchTarget& target, ptycho_plan_t** out);
 // Evaluations per position batch of a served site, in both tick forms.  Measured on the
 // 64-request serving stream: per-site graphs 576 / 649 / 659 K evals/s with 128 / 600 / 1200;
 // shared launches 468 / 500 / 519 / 524 K with 300 / 600 / 1200 / 2400.  1200 is also the
 // single-site default, so a site's scratch is what its own plan would take.
 constexpr long long kServeBatchEvals = 1200;
+constexpr BatchTarget kServeBatchTarget{kServeBatchEvals, 1, 2ll << 30};
 
 // Object regulariser (reg.cu): adds R to *loss (if not null) and dR to gO on stream st.
 bool reg_args_ok(float mu_l1, float mu_tv, float eta);

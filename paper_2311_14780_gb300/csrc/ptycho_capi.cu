@@ -153,8 +153,16 @@ using ptycho::CallKind;
 
 namespace {
 
-constexpr long long kMaxScratch = 2ll << 30;   // default upper bound of the FFT scratch
+// The default batching: about kBatchEvals evaluations per batch, but at least kMinBatchPositions
+// positions, one buffer set of at most kMaxScratch.  Measured on 512^2 x 6 wavelengths x 10
+// modes (120 MB of fields per position), where the per-batch work that does not grow with the
+// batch (reading the probes in the forward and adjoint rows, adding into the probe gradient,
+// the launches' tails) is largest: 17 / 20 / 26 / 34 / 45 / 60 / 75 / 100 positions per batch
+// gave 143.0 / 141.5 / 140.3 / 138.7 / 137.0 / 136.1 / 135.6 / 134.8 ms per step (three batches
+// in flight); 512^2 x 8 modes x 5 wavelengths: 41.8 ms with 25 positions, 40.9 with 58.
+constexpr long long kMaxScratch = 8ll << 30;   // default upper bound of one buffer set
 constexpr long long kBatchEvals = 1200;        // evaluations per batch the default aims for
+constexpr long long kMinBatchPositions = 64;   // and at least this many positions (when they fit)
 constexpr long long kMinBatches = 3;           // and at least this many batches per call (overlap)
 constexpr long long kBatchRows = 32768;        // and at least this many 1D FFT rows per pass
 constexpr int kDefaultOverlap = 3;             // position batches in flight
@@ -443,14 +451,14 @@ const char* ptycho_strerror(int code) {
 }
 
 int ptycho_plan_create(const ptycho_geom_t* g, ptycho_plan_t** out) {
-  return ptycho::create_plan(g, kBatchEvals, out);
+  return ptycho::create_plan(g, ptycho::BatchTarget{kBatchEvals, kMinBatchPositions, kMaxScratch}, out);
 }
 
 }  // extern "C"
 
 namespace ptycho {
 
-int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** out) {
+int create_plan(const ptycho_geom_t* g, const BatchTarget& target, ptycho_plan_t** out) {
   if (!g || !out) return PTYCHO_EINVAL;
   *out = nullptr;
   if (g->L < 1 || g->M < 1 || g->J < 1 || !g->obj_h || !g->obj_w || !g->pos) return PTYCHO_EINVAL;
@@ -512,18 +520,23 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
   // positions as the budget holds.
   const long long FF8 = (long long)F * F * (long long)sizeof(float2);
   const long long LM = (long long)g->L * g->M;
-  p->scratch_budget = g->scratch_bytes > 0 ? g->scratch_bytes : kMaxScratch;
+  p->scratch_budget = g->scratch_bytes > 0 ? g->scratch_bytes : target.max_set_bytes;
   if (LM * FF8 <= p->scratch_budget) {
     p->store = 1;
     p->C = (int)LM;
     p->nchunks = 1;
     long long B = p->scratch_budget / (LM * FF8);
     if (g->scratch_bytes <= 0) {
-      B = std::min<long long>(B, std::max((batch_evals + LM - 1) / LM, (kBatchRows + LM * F - 1) / (LM * F)));
+      B = std::min<long long>(B, std::max({(target.evals + LM - 1) / LM, (kBatchRows + LM * F - 1) / (LM * F),
+                                           target.min_positions}));
       B = std::min<long long>(B, std::max<long long>(1, (g->J + kMinBatches - 1) / kMinBatches));
     }
     p->B = (int)std::max<long long>(1, std::min<long long>(B, ptycho::kMaxB));
     p->B = std::min(p->B, g->J);
+    if (g->scratch_bytes <= 0) {                      // the same number of batches, sizes within one position
+      const int nbat = (g->J + p->B - 1) / p->B;
+      p->B = (g->J + nbat - 1) / nbat;
+    }
   } else {
     p->store = 0;
     p->B = 1;
@@ -537,8 +550,8 @@ int create_plan(const ptycho_geom_t* g, long long batch_evals, ptycho_plan_t** o
     case 256: colblocks = F / ptycho::ColCfg<256>::W; break;
     default: colblocks = F / ptycho::ColCfg<512>::W; break;
   }
-  const long long target = 2ll * p->sms;   // column blocks wanted: mode groups only below two per SM
-  long long G = (target + (long long)colblocks * p->B - 1) / ((long long)colblocks * p->B);
+  const long long want_cols = 2ll * p->sms;   // column blocks wanted: mode groups only below two per SM
+  long long G = (want_cols + (long long)colblocks * p->B - 1) / ((long long)colblocks * p->B);
   if (g->col_groups > 0) G = g->col_groups;
   G = std::max<long long>(1, std::min<long long>(G, p->C));
   p->MG = (int)((p->C + G - 1) / G);

@@ -548,9 +548,9 @@ int ptycho_server_admit(ptycho_server_t* sv, const ptycho_geom_t* geom, const pt
     g.col_groups = 0;
     g.zoom = nullptr;
     if (geom->zoom || geom->flags) { delete s; return PTYCHO_EUNSUPPORTED; }
-    rc = ptycho::create_plan(&g, ptycho::kServeBatchEvals, &s->plan);
+    rc = ptycho::create_plan(&g, ptycho::kServeBatchTarget, &s->plan);
   } else {
-    rc = ptycho::create_plan(geom, ptycho::kServeBatchEvals, &s->plan);
+    rc = ptycho::create_plan(geom, ptycho::kServeBatchTarget, &s->plan);
   }
   if (rc) { delete s; return rc; }
   ptycho_plan* p = s->plan;
