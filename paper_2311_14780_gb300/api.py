@@ -17,11 +17,25 @@ import torch
 from . import _native
 
 LOSS_CODES = {"amplitude": 0, "poisson": 1, "poisson_gaussian": 2}
+# pipeline variants (PTYCHO_FLAG_* in include/ptycho.h, where each is described)
 FLAG_RECOMPUTE_COLUMNS = 1
 FLAG_OBJ_GRAD_ATOMIC = 2
 FLAG_KEEP_PSI = 4
 FLAG_NO_TMA = 8
 FLAG_TMA = 16
+FLAG_UNFUSED_ROW_ADJ = 32
+FLAG_STAGED_COLUMNS = 64
+FLAG_NARROW_COLUMNS = 128
+FLAG_FUSED_ROW_FWD = 256
+FLAG_NO_PDL = 512
+FLAG_RESIDENT_FRAMES = 1024
+FLAG_ROW_ADJ_PROBE_L2 = 2048
+FLAG_ROW_ADJ_PROBE_SMEM = 4096
+FLAG_UNFUSED_ROW_FWD = 8192
+FLAG_ROWS_16_THREADS = 16384
+FLAG_FWD_ROWS_WARP = 32768
+FLAG_COLS_ONE_BLOCK = 65536
+FLAG_FUSED_ROW_ADJ = 131072
 
 
 class PtychoError(RuntimeError):

@@ -45,6 +45,17 @@ def test_binding_declares_every_exported_symbol():
     assert set(declared_symbols()) <= bound | {"ptycho_plan_create"}
 
 
+def test_python_flag_constants_match_the_header():
+    from paper_2311_14780_gb300 import api
+    text = open(HEADER).read()
+    flags = dict((k, int(v)) for k, v in re.findall(r"#define PTYCHO_FLAG_([A-Z0-9_]+) (\d+)", text))
+    assert flags
+    for name, value in flags.items():
+        assert getattr(api, "FLAG_" + name) == value, name
+    assert len(set(flags.values())) == len(flags)                          # distinct bits
+    assert all(v & (v - 1) == 0 for v in flags.values())
+
+
 def test_strerror(lib):
     assert lib.ptycho_strerror(0) == b"success"
     assert b"outside" in lib.ptycho_strerror(-2)
